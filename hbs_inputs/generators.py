@@ -1,0 +1,167 @@
+"""Input generators (see the package docstring). No compression arithmetic lives here."""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 220502990
+
+
+def seed_for(workload, role):
+    """Deterministic seed per (workload number, role): 0 Omega, 1 Psi, 2 generator, 3 probe."""
+    return BASE_SEED + 100 * int(workload) + int(role)
+
+
+def gaussian(shape, seed):
+    """i.i.d. standard normal float64 array."""
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
+@dataclass
+class CurvePoints:
+    x: np.ndarray
+    y: np.ndarray
+
+
+def curve_points(N):
+    """N points at theta_i = 2 pi i / N on r(theta) = 1 + 0.3 cos(5 theta)."""
+    theta = 2.0 * np.pi * np.arange(N, dtype=np.float64) / N
+    rad = 1.0 + 0.3 * np.cos(5.0 * theta)
+    return CurvePoints(rad * np.cos(theta), rad * np.sin(theta))
+
+
+def log_kernel_rows(N, rows, cols=None):
+    """Rows ``rows`` (and columns ``cols``, default all) of the dense log kernel, float64."""
+    p = curve_points(N)
+    rows = np.asarray(rows)
+    cols = np.arange(N) if cols is None else np.asarray(cols)
+    dx = p.x[rows][:, None] - p.x[cols][None, :]
+    dy = p.y[rows][:, None] - p.y[cols][None, :]
+    d = np.hypot(dx, dy)
+    same = rows[:, None] == cols[None, :]
+    with np.errstate(divide="ignore"):
+        out = np.log(np.where(same, 1.0, d))
+    out[same] = 0.0
+    return out
+
+
+def log_kernel(N):
+    """Dense N x N log kernel, float64 (small N only: N^2 doubles on the host)."""
+    return log_kernel_rows(N, np.arange(N))
+
+
+def log_kernel_torch(N, device, dtype=None, row_block=4096):
+    """Dense N x N log kernel built by torch on ``device`` (float64 arithmetic, then cast).
+
+    Built in row blocks so that the float64 temporaries stay small next to the result.
+    """
+    import torch
+    dtype = dtype or torch.float64
+    p = curve_points(N)
+    x = torch.as_tensor(p.x, device=device)
+    y = torch.as_tensor(p.y, device=device)
+    A = torch.empty((N, N), dtype=dtype, device=device)
+    for r0 in range(0, N, row_block):
+        r1 = min(N, r0 + row_block)
+        d = torch.hypot(x[r0:r1, None] - x[None, :], y[r0:r1, None] - y[None, :])
+        idx = torch.arange(r0, r1, device=device)
+        d[idx - r0, idx] = 1.0
+        blk = torch.log(d)
+        blk[idx - r0, idx] = 0.0
+        A[r0:r1] = blk.to(dtype)
+        del d, blk
+    return A
+
+
+def _tree(N, leaf_max):
+    """Section 3.1 tree: (L, offsets, sizes) by node id (1-based heap numbering)."""
+    sizes = [N]
+    L = 0
+    while max(sizes) > leaf_max:
+        sizes = [h for n in sizes for h in ((n + 1) // 2, n // 2)]
+        L += 1
+    offsets = [0] * 2 ** (L + 1)
+    sz = [0] * 2 ** (L + 1)
+    sz[1] = N
+    for t in range(1, 2 ** L):
+        left = (sz[t] + 1) // 2
+        offsets[2 * t], sz[2 * t] = offsets[t], left
+        offsets[2 * t + 1], sz[2 * t + 1] = offsets[t] + left, sz[t] - left
+    return L, offsets, sz
+
+
+def _orthonormal(rng, n, k):
+    q, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    return q
+
+
+@dataclass
+class ExactHBS:
+    """Exact-rank HBS matrix: classical generators plus telescoping factors (node ids 1-based)."""
+    N: int
+    k: int
+    L: int
+    offsets: list
+    sizes: list
+    U: dict = field(default_factory=dict)        # levels 1..L
+    V: dict = field(default_factory=dict)
+    D: dict = field(default_factory=dict)        # leaves: diagonal block; parents/root: [[0,B],[B',0]]
+    B: dict = field(default_factory=dict)        # (alpha, beta) -> k x k coupling
+
+    def dense(self):
+        """Assemble A block by block: A(I_a, I_b) = Ubar_a B_ab Vbar_b^T for siblings a != b,
+        leaf diagonal blocks D; Ubar is the expanded basis (leaf U, or blockdiag of the
+        children's expanded bases times the node's U)."""
+        N, L = self.N, self.L
+        if L == 0:
+            return self.D[1].copy()
+        Ubar, Vbar = {}, {}
+        for level in range(L, 0, -1):
+            for t in range(2 ** level, 2 ** (level + 1)):
+                if level == L:
+                    Ubar[t], Vbar[t] = self.U[t], self.V[t]
+                else:
+                    a, b = 2 * t, 2 * t + 1
+                    Ubar[t] = np.vstack([Ubar[a] @ self.U[t][:self.k], Ubar[b] @ self.U[t][self.k:]])
+                    Vbar[t] = np.vstack([Vbar[a] @ self.V[t][:self.k], Vbar[b] @ self.V[t][self.k:]])
+        A = np.zeros((N, N))
+        for t in range(2 ** L, 2 ** (L + 1)):
+            o, n = self.offsets[t], self.sizes[t]
+            A[o:o + n, o:o + n] = self.D[t]
+        for t in range(1, 2 ** L):
+            a, b = 2 * t, 2 * t + 1
+            ia = slice(self.offsets[a], self.offsets[a] + self.sizes[a])
+            ib = slice(self.offsets[b], self.offsets[b] + self.sizes[b])
+            A[ia, ib] = Ubar[a] @ self.B[(a, b)] @ Vbar[b].T
+            A[ib, ia] = Ubar[b] @ self.B[(b, a)] @ Vbar[a].T
+        return A
+
+
+def exact_hbs(N, leaf_max, k, seed):
+    """Random HBS matrix of exact block rank k on the Section 3.1 tree with threshold leaf_max."""
+    rng = np.random.default_rng(seed)
+    L, offsets, sizes = _tree(N, leaf_max)
+    g = ExactHBS(N=N, k=k, L=L, offsets=offsets, sizes=sizes)
+    if L == 0:
+        g.D[1] = rng.standard_normal((N, N))
+        return g
+    for t in range(2 ** L, 2 ** (L + 1)):
+        n = sizes[t]
+        if n < k:
+            raise ValueError("leaf smaller than k")
+        g.U[t] = _orthonormal(rng, n, k)
+        g.V[t] = _orthonormal(rng, n, k)
+        g.D[t] = rng.standard_normal((n, n))
+    for level in range(L - 1, 0, -1):
+        for t in range(2 ** level, 2 ** (level + 1)):
+            g.U[t] = _orthonormal(rng, 2 * k, k)
+            g.V[t] = _orthonormal(rng, 2 * k, k)
+    for t in range(1, 2 ** L):
+        a, b = 2 * t, 2 * t + 1
+        g.B[(a, b)] = rng.standard_normal((k, k))
+        g.B[(b, a)] = rng.standard_normal((k, k))
+        Dt = np.zeros((2 * k, 2 * k))
+        Dt[:k, k:] = g.B[(a, b)]
+        Dt[k:, :k] = g.B[(b, a)]
+        g.D[t] = Dt
+    return g
