@@ -1,0 +1,377 @@
+"""Benchmark: one step = one pass of black-box HBS compression (Algorithm 2) on one matrix.
+
+Workload (default): dense 2D log kernel A_ij = log|x_i - x_j| (A_ii = 0) on N = 32768 points
+evenly spaced in angle on r(theta) = 1 + 0.3 cos 5 theta, rank parameter r = 40, s = 120 test
+vectors, leaf size 64 (the largest power-of-two split with leaf <= s - r), all in FP64.
+A step draws Omega and Psi (Philox, 2 launches), forms Y = A Omega and Z = A^* Psi (2 FP64
+GEMM launches) and runs the sweep (one launch per tree level, 10 levels). A (8.6 GB) is
+resident in HBM before timing and is streamed in full every step, so no L2 flush is needed.
+
+Metric: compress throughput N*s / T (sample rows x columns consumed per second) with the
+compress time T in ms_per_step. ``e2e`` repeats the step through the same C ABI calls with A in
+pinned host memory, copying A in and the factors out inside the timed region. ``cpu_baseline``
+and ``--impl reference`` time the FP64 oracle on the host cores on a bounded sample of the same
+workload (stated in the ``sample`` field) and scale it to the full workload.
+
+Multi-GPU (torchrun): each rank compresses its own replica; ranks never exchange data.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HBS compress time (ms) & N·s/sec at stated rel. error, mixed/batched vs FP64"
+UNIT = "N*s/s"
+N_DEF, R_DEF, S_DEF, LEAF_DEF, SEED = 32768, 40, 120, 64, 220502990 + 200
+SM_COUNT_GB300 = 152
+FP64_DFMA_PER_CLK_PER_SM = 2          # GB300: FP64 at 1/64 of the FP32 rate (1.25 TF nominal)
+FP64_PROBE_TFLOPS = 1.056             # measured DFMA throughput on this GB300 (see profiles/)
+GEMM_TRAFFIC_8192 = 550.9e6           # dram read+write of one sample_gemm_f64 launch, N = 8192
+
+
+def tree_nodes(N, leaf):
+    L = 0
+    while -(-N // 2 ** L) > leaf:
+        L += 1
+    return L
+
+
+def node_flops(n, r, s, root=False):
+    """Algorithmic FP64 flops of one node of the sweep (Householder counts)."""
+    lq = 2 * n * n * (s - n / 3)                 # QR of Omega_tau^* (s x n)
+    stream = 4 * n * n * s - 2 * n ** 3          # n rows through n reflectors
+    solve = n ** 3                               # rows of Y Omega^+ against L_1
+    if root:
+        return lq + stream + solve
+    colqr = 2 * r * r * (n - r / 3) + 4 * n * r * r - 4 * r ** 3 / 3
+    dblk = 12 * r * n * n
+    merge = 12 * n * r * s
+    return 2 * (lq + stream + solve + colqr) + dblk + merge
+
+
+def sweep_flops(N, r, s, leaf):
+    L = tree_nodes(N, leaf)
+    total = 0.0
+    for level in range(L, -1, -1):
+        cnt = 2 ** level
+        if level == L and L > 0:
+            big = -(-N // 2 ** L)
+            small = N // 2 ** L
+            n_big = N - small * cnt
+            total += n_big * node_flops(big, r, s) + (cnt - n_big) * node_flops(small, r, s)
+        elif level == 0:
+            total += node_flops(2 * r if L > 0 else N, r, s, root=True)
+        else:
+            total += cnt * node_flops(2 * r, r, s)
+    return total
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload (cpu_baseline and --impl reference)
+
+def oracle_sample_time(N, r, s, leaf, rows=4096, sweep_N=8192):
+    """Seconds the FP64 oracle would take for the full workload, from a bounded sample:
+    Philox rows and sampling products for ``rows`` of the N rows, and the sweep of a
+    ``sweep_N``-point problem of the same r, s, leaf, each scaled by its share of the work."""
+    import numpy as np
+    from hbs_inputs import gaussian, log_kernel_rows
+    from oracle import philox
+    from oracle.compress import compress
+    from oracle.sample import sample_dense
+
+    idx = np.arange(rows)
+    A_rows = log_kernel_rows(N, idx)                         # input, not timed
+    t0 = time.perf_counter()
+    Om_rows = philox.gaussian_matrix(N, s, 0, SEED, rows=idx)
+    Ps_rows = philox.gaussian_matrix(N, s, 1, SEED, rows=idx)
+    t_rng = (time.perf_counter() - t0) * N / rows
+    Om = np.tile(Om_rows, (N // rows + 1, 1))[:N]           # full-height Omega stand-in
+    t0 = time.perf_counter()
+    sample_dense(A_rows, Om, Ps_rows)                        # rows x N block of both products
+    t_smp = (time.perf_counter() - t0) * N / rows
+    x = [gaussian((sweep_N, s), 17 + i) for i in range(4)]
+    t0 = time.perf_counter()
+    compress(*x, r, leaf)
+    t_sw = (time.perf_counter() - t0) * sweep_flops(N, r, s, leaf) / sweep_flops(sweep_N, r, s, leaf)
+    sample = (f"Philox draws and both sampling products for {rows} of {N} rows, sweep of a "
+              f"{sweep_N}-point problem (r={r}, s={s}, leaf {leaf}); scaled to N={N} by rows and "
+              f"by sweep flops")
+    return t_rng + t_smp + t_sw, sample
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, N, r, s, leaf):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_time(N, r, s, leaf)
+    times, sample = [], ""
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        t, sample = oracle_sample_time(N, r, s, leaf)
+        times.append(t)
+    wall = time.perf_counter() - wall0
+    t = statistics.mean(times)
+    value = N * s / t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"log-kernel N={N} r={r} s={s} leaf={leaf} FP64 dense",
+                       "N": N, "r": r, "s": s, "leaf": leaf, "precision": "fp64",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample, "wall_s": wall},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hbs", choices=["hbs", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    N, r, s, leaf = args.N, R_DEF, S_DEF, LEAF_DEF
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, N, r, s, leaf)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2205_02990_gb300 as hb
+    from hbs_inputs import log_kernel_torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hb.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    A = log_kernel_torch(N, "cuda")
+    Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
+    prob = hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)
+    h = hb.hbs_plan([prob])
+    L = tree_nodes(N, leaf)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    seed = SEED + 1000 * rank
+
+    def step(i=None, A_op=A):
+        hb.hbs_draw_gaussian(N, s, 0, seed, Om)
+        hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
+        if i is not None:
+            ev[i][0].record(stream)
+        hb.hbs_sample_products(A_op, s, Om, Ps, Y, Z)
+        if i is not None:
+            ev[i][1].record(stream)
+        hb.hbs_execute(h, [prob])
+
+    for _ in range(args.warmup):
+        step()
+    hb.hbs_sync_status(h)
+    barrier()
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    gpu_id = visible[local].strip() if local < len(visible) and visible[local].strip() else local
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        start.record(stream)
+        for i in range(args.steps):
+            step(i)
+        stop.record(stream)
+        barrier()
+    elapsed = start.elapsed_time(stop) / 1e3
+    gemm_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * args.steps)   # per launch
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    hb.hbs_sync_status(h)
+    clocks = clk.summary()
+
+    # accuracy of the compressed operator: 20-step power iteration (Section 5), on the GPU
+    def power_norm(apply_B, apply_Bt, steps=20):
+        g = torch.Generator(device="cuda").manual_seed(3)
+        v = torch.randn((N, 1), dtype=torch.float64, device="cuda", generator=g)
+        for _ in range(steps):
+            v = apply_Bt(apply_B(v / torch.linalg.norm(v)))
+        return float(torch.sqrt(torch.linalg.norm(v)))
+
+    def apply_h(x, trans=False):
+        out = torch.empty_like(x)
+        hb.hbs_apply(h, x, out, trans=trans)
+        return out
+
+    rel_err = None
+    if not args.no_accuracy:
+        nA = power_norm(lambda x: A @ x, lambda x: A.T @ x)
+        nE = power_norm(lambda x: apply_h(x) - A @ x, lambda x: apply_h(x, True) - A.T @ x)
+        rel_err = nE / nA
+
+    # end to end through the C ABI with host buffers: A in, factors out, every step
+    e2e = None
+    if not args.no_e2e:
+        A_host = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
+        A_host.copy_(A)
+        F_host = torch.empty(hb.hbs_factor_bytes(h), dtype=torch.uint8, pin_memory=True)
+        A_dev2 = torch.empty_like(A)
+        del A
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            A_dev2.copy_(A_host, non_blocking=True)
+            step(None, A_dev2)
+            hb.hbs_copy_factors(h, F_host)
+
+        e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        te = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * N * s * args.steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": hb.hbs_factor_bytes(h)}
+
+    value = world * N * s * args.steps / elapsed
+    flops_gemm = 2.0 * N * N * s                            # one of the two products
+    fp64_peak = SM_COUNT_GB300 * FP64_DFMA_PER_CLK_PER_SM * 2 * 2070e6 / 1e12
+    achieved = flops_gemm / gemm_s / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"log-kernel N={N} r={r} s={s} leaf={leaf} FP64 dense",
+                   "N": N, "r": r, "s": s, "leaf": leaf, "levels": L + 1, "precision": "fp64",
+                   "l2": "inputs larger than L2 (A = %.1f GB streamed every step)" % (N * N * 8 / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "rel_error": {"opnorm_power20": rel_err, "vs": "dense A"},
+        "compress_ms": elapsed / args.steps * 1e3,
+        "sweep_gflop": sweep_flops(N, r, s, leaf) / 1e9,
+        "gpu_launches": args.steps * (2 + 2 + (L + 1)),
+        "roofline": {"kernel": "sample_gemm_f64 (Y = A Omega, Z = A^T Psi)", "bound": "alu",
+                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": GEMM_TRAFFIC_8192 * (N / 8192) ** 2,
+                     "traffic_source": "ncu capture at N=8192 scaled by (N/8192)^2",
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
+                     "probe_peak": FP64_PROBE_TFLOPS},
+        "clocks": clocks,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_cpu, sample = oracle_sample_time(N, r, s, leaf)
+        line["cpu_baseline"] = {"value": N * s / t_cpu, "unit": UNIT, "cores": cpu_cores(),
+                                "kind": "oracle", "sample": sample}
+    h.free()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

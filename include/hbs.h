@@ -1,0 +1,190 @@
+/*
+ * hbs.h -- C ABI of the GB300 library for black-box randomized compression of HBS matrices
+ * (Levitt & Martinsson, "Linear-Complexity Black-Box Randomized Compression of
+ * Rank-Structured Matrices").
+ *
+ * The problem (Section 1): an N x N matrix A is reachable only through products X -> A X and
+ * X -> A^* X. Draw Gaussian test matrices Omega, Psi (N x s), form the samples Y = A Omega and
+ * Z = A^* Psi, and recover from {Y, Omega, Z, Psi} the telescoping factorization of Section
+ * 3.3 (bases U_tau, V_tau and discrepancy blocks D_tau on the tree of Section 3.1) by the
+ * level-by-level sweep of Algorithm 2. The factorization is applied by Algorithm 1.
+ *
+ * Conventions for every call below:
+ *  - Real matrices only; "*" is the transpose (Section 2.1).
+ *  - Every matrix argument is ROW-MAJOR with the leading dimension stated. Unless a call says
+ *    otherwise, array pointers are DEVICE pointers on the current CUDA device.
+ *  - The caller owns every input and output buffer and keeps it alive until the work queued on
+ *    `cuda_stream` (a cudaStream_t; NULL = legacy default stream) has finished.
+ *  - Calls are asynchronous on `cuda_stream` unless stated. Argument and shape errors are
+ *    detected on the host before anything is queued or allocated and are returned at once.
+ *  - Numerical failures found on the device (a zero or non-finite pivot of a triangular
+ *    factor) are recorded in a per-handle status word, read by hbs_sync_status().
+ *  - Every non-OK return leaves a message for hbs_last_error() (per calling thread).
+ *  - The tree is the one of Section 3.1: root I = [0, N); the left child of a node of n
+ *    indices receives the first ceil(n/2); nodes are split while larger than leaf_max, all
+ *    leaves sit on level L; node ids follow Fig. 1 (root 1, children 2t and 2t+1).
+ */
+#ifndef HBS_H
+#define HBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HBS_OK = 0,
+  HBS_ERR_ARG = -1,         /* NULL pointer, non-positive size, bad enum, item out of range */
+  HBS_ERR_SHAPE = -2,       /* (N, r, s, leaf_max) not admissible, see hbs_compress */
+  HBS_ERR_NOMEM = -3,       /* device allocation failed */
+  HBS_ERR_CUDA = -4,        /* a CUDA runtime call failed (message has the CUDA error) */
+  HBS_ERR_NUMERIC = -5,     /* zero or non-finite diagonal of a triangular factor */
+  HBS_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+  HBS_ERR_CALLBACK = -7,    /* the black-box operator callback returned non-zero */
+  HBS_ERR_UNSUPPORTED = -8  /* valid request outside what this build implements */
+} hbs_status;
+
+typedef enum {
+  HBS_PREC_FP64 = 0         /* every step in IEEE binary64 on the FP64 pipe */
+} hbs_precision;
+
+typedef enum { HBS_F64 = 0, HBS_F32 = 1 } hbs_dtype;
+
+/* ---------------------------------------------------------------------------------------
+ * Test matrices (Algorithm 2, first block; Section 2.3, step 2).
+ * Fills out[0 .. N*s) (row-major N x s) with i.i.d. standard normals from the counter-based
+ * generator Philox4x32-10 (Salmon et al., SC'11) and the Box-Muller transform:
+ *   element e = i*s + j belongs to pair p = e / 2; counter = (p mod 2^32, p div 2^32,
+ *   stream_id, 0), key = (seed mod 2^32, seed div 2^32); with output words x0..x3,
+ *   u1 = (top 52 bits of x0*2^32+x1 + 1/2) 2^-52, u2 likewise from x2, x3,
+ *   element 2p = sqrt(-2 ln u1) cos(2 pi u2), element 2p+1 = sqrt(-2 ln u1) sin(2 pi u2).
+ * stream_id 0 draws Omega and 1 draws Psi in hbs_sample. out: device, FP64.
+ * Errors: HBS_ERR_ARG (out NULL, N < 1 or s < 1), HBS_ERR_CUDA.
+ */
+int hbs_draw_gaussian(int64_t N, int32_t s, uint32_t stream_id, uint64_t seed, double* out,
+                      void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * The black-box operator (Section 1): either a dense matrix or a callback.
+ * Dense: A != NULL, row-major N x N with leading dimension lda >= N, element type `dtype`
+ *   (only HBS_F64 in this build), device memory.
+ * Callback: A == NULL and fn != NULL. fn(user, trans, N, ncols, X, Out, cuda_stream) must
+ *   queue Out = A X (trans = 0) or Out = A^* X (trans = 1) on cuda_stream, X and Out row-major
+ *   N x ncols FP64 device arrays, and return 0 (any other value gives HBS_ERR_CALLBACK).
+ */
+typedef int (*hbs_matmat_fn)(void* user, int trans, int64_t N, int32_t ncols, const double* X,
+                             double* Out, void* cuda_stream);
+
+typedef struct {
+  int64_t N;
+  int32_t dtype;
+  const void* A;
+  int64_t lda;
+  hbs_matmat_fn fn;
+  void* user;
+} hbs_operator;
+
+/* Randomized samples (Algorithm 2, first block): draws Omega (stream 0) and Psi (stream 1)
+ * from `seed` as hbs_draw_gaussian does, then Y = A Omega and Z = A^* Psi.
+ * Omega, Psi, Y, Z: device, FP64, row-major N x s (leading dimension s), written.
+ * Errors: HBS_ERR_ARG, HBS_ERR_UNSUPPORTED (precision or dtype), HBS_ERR_CALLBACK, HBS_ERR_CUDA.
+ */
+int hbs_sample(const hbs_operator* op, int32_t s, uint64_t seed, int32_t precision,
+               double* Omega, double* Psi, double* Y, double* Z, void* cuda_stream);
+
+/* The products alone, for test matrices the caller already holds (Algorithm 2, "Multiply
+ * Y = A Omega and Z = A^* Psi"): Omega, Psi read, Y, Z written; all device FP64 row-major
+ * N x s. Same operator rules and errors as hbs_sample. */
+int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, const double* Omega,
+                        const double* Psi, double* Y, double* Z, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
+ * One compression problem: test matrices and samples of one N x N matrix.
+ * Omega, Psi, Y, Z: device, FP64, row-major N x s, leading dimension s.
+ * r: rank parameter r = k + p of Section 4 (block rank plus oversampling).
+ */
+typedef struct {
+  int64_t N;
+  int32_t r;
+  int32_t s;
+  int32_t leaf_max;
+  const double* Omega;
+  const double* Psi;
+  const double* Y;
+  const double* Z;
+} hbs_problem;
+
+typedef struct hbs_handle hbs_handle;   /* opaque: owns the factors and all workspace */
+
+/* Plan a batch of compressions: validates every problem, builds every tree and allocates the
+ * device arena for the factors and workspace. Queues no work. Admissible shapes (Section 4
+ * asks for s >= max(r + m, 3r)): with L >= 1, every leaf has between r and s - r rows and
+ * s >= 3r; with L = 0 (N <= leaf_max), N <= s. This build also needs the per-node shared-memory
+ * tile to fit: n (s + 1) + r n <= 28672 doubles for every node of n rows (s <= ~160 at r = 50).
+ * Errors: HBS_ERR_ARG, HBS_ERR_SHAPE, HBS_ERR_UNSUPPORTED, HBS_ERR_NOMEM, HBS_ERR_CUDA.
+ */
+int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out);
+
+/* Run Algorithm 2 for every problem of a planned handle on `cuda_stream`. `probs` must have
+ * the same batch size and shapes as at planning; its pointers may differ. The factors of the
+ * previous execution are overwritten.
+ * Errors: HBS_ERR_ARG (NULL, shape differs from the plan), HBS_ERR_CUDA.
+ */
+int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream);
+
+/* hbs_plan followed by hbs_execute. */
+int hbs_compress(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out,
+                 void* cuda_stream);
+
+/* Algorithm 1: Out = A~ X (trans = 0) or A~^* X (trans = 1) for the compressed form of problem
+ * `item` of the handle. X, Out: device, FP64, row-major N x ncols, leading dimension ncols,
+ * must not overlap. The handle keeps a workspace of 2 (2^(L+1) - 2) r ncols doubles, grown
+ * (by cudaMalloc, on the first call that needs more) and reused.
+ * Errors: HBS_ERR_ARG, HBS_ERR_NOMEM, HBS_ERR_CUDA.
+ */
+int hbs_apply(hbs_handle* h, int32_t item, int trans, int32_t ncols, const double* X,
+              double* Out, void* cuda_stream);
+
+/* Waits for the handle's queued work (cudaStreamSynchronize on cuda_stream) and returns the
+ * device status of its last execution: HBS_OK or HBS_ERR_NUMERIC. Clears the status word. */
+int hbs_sync_status(hbs_handle* h, void* cuda_stream);
+
+/* Frees the handle and everything it owns (NULL-safe). The caller must make sure no queued
+ * work still uses it. */
+void hbs_free(hbs_handle* h);
+
+/* Message for the last non-OK status returned to the calling thread ("" if none). */
+const char* hbs_last_error(void);
+
+/* ---------------------------------------------------------------------------------------
+ * Introspection (for tests and tools; synchronous, not on any hot path).
+ */
+
+/* Depth L and, when the arrays are non-NULL, the 0-based offsets and sizes of nodes
+ * 1 .. 2^(L+1) - 1 of problem `item` written at indices 0 .. 2^(L+1) - 2 (host arrays of at
+ * least 2^(L+1) - 1 entries). */
+int hbs_tree(const hbs_handle* h, int32_t item, int32_t* L, int64_t* offsets, int64_t* sizes);
+
+/* Tree of Section 3.1 without a handle: same output as hbs_tree; max_nodes bounds the arrays.
+ * Errors: HBS_ERR_ARG (N < 1, leaf_max < 1, arrays too small). */
+int hbs_tree_build(int64_t N, int32_t leaf_max, int32_t* L, int64_t* offsets, int64_t* sizes,
+                   int64_t max_nodes);
+
+/* Copies the factors of node `node` (Fig. 1 numbering) of problem `item`: U and V (n x r) for
+ * nodes on levels 1..L, D (n x n; for the root n = 2r, or N when L = 0). Destination pointers
+ * may be host or device (any may be NULL to skip). Waits for the device. Row-major. */
+int hbs_get_node(const hbs_handle* h, int32_t item, int64_t node, int32_t* n, double* U,
+                 double* V, double* D);
+
+/* Total bytes of all factors of the handle, and an asynchronous copy of them to `dst` (host
+ * or device) in the handle's arena order: per item, per node id 1.., U, V then D. */
+size_t hbs_factor_bytes(const hbs_handle* h);
+int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBS_H */

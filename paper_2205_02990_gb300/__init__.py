@@ -1,0 +1,16 @@
+"""GB300 black-box randomized compression of HBS matrices (Levitt & Martinsson).
+
+The computation lives in ``lib/libhbs.so`` (CUDA for sm_103a, C ABI in ``include/hbs.h``);
+``paper_2205_02990_gb300.hbs`` is its thin Python binding. Build with
+``python -m paper_2205_02990_gb300.build``.
+"""
+
+from .hbs import (HBS_PREC_FP64, Handle, HBSError, Problem, hbs_apply, hbs_compress,
+                  hbs_copy_factors, hbs_draw_gaussian, hbs_execute, hbs_factor_bytes, hbs_free,
+                  hbs_get_node, hbs_plan, hbs_sample, hbs_sample_products, hbs_sync_status, hbs_tree, hbs_tree_build,
+                  load)
+
+__all__ = ["HBS_PREC_FP64", "Handle", "HBSError", "Problem", "hbs_apply", "hbs_compress",
+           "hbs_copy_factors", "hbs_draw_gaussian", "hbs_execute", "hbs_factor_bytes", "hbs_free",
+           "hbs_get_node", "hbs_plan", "hbs_sample", "hbs_sample_products", "hbs_sync_status", "hbs_tree",
+           "hbs_tree_build", "load"]

@@ -1,0 +1,560 @@
+// C ABI of include/hbs.h: argument checks, the Section 3.1 tree, the device arena, the
+// per-level work lists of Algorithm 2 and Algorithm 1, and the launches.
+//
+// Arena layout (doubles), one allocation per handle:
+//   [factors]   per item, per node id 1..2^(L+1)-1: U (n x r), V (n x r) for levels >= 1,
+//               then D (n x n; root: 2r x 2r, or N x N when L = 0)
+//   [workspace] per item, per node on levels >= 1: Y Omega^+ and Z Psi^+ (n x n each)
+//   [blocks]    per item, per node on levels 0..L-1: the node's Omega, Psi, Y, Z blocks
+//               (2r x s each), filled by its children (Eq. omega_tau_and_y_tau)
+// Work lists: height t = L_i - level groups level L_i - t of every item, so one launch per
+// height covers a whole batch of trees of different depths; heights run finest first.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hbs.h"
+#include "hbs_internal.cuh"
+
+using hbs::GemmTask;
+using hbs::NodeTask;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(HBS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int ok() {
+  g_last_error.clear();
+  return HBS_OK;
+}
+
+// Section 3.1 tree: depth, offsets and sizes indexed by node id (entry 0 unused).
+void build_tree(int64_t N, int64_t leaf_max, int* L, std::vector<int64_t>* off,
+                std::vector<int64_t>* size) {
+  int depth = 0;
+  while (true) {
+    const int64_t biggest = (N + (int64_t(1) << depth) - 1) >> depth;   // ceil(N / 2^depth)
+    if (biggest <= leaf_max) break;
+    ++depth;
+  }
+  const int64_t count = int64_t(1) << (depth + 1);
+  off->assign(count, 0);
+  size->assign(count, 0);
+  (*size)[1] = N;
+  for (int64_t t = 1; t < (int64_t(1) << depth); ++t) {
+    const int64_t left = ((*size)[t] + 1) / 2;
+    (*off)[2 * t] = (*off)[t];
+    (*size)[2 * t] = left;
+    (*off)[2 * t + 1] = (*off)[t] + left;
+    (*size)[2 * t + 1] = (*size)[t] - left;
+  }
+  *L = depth;
+}
+
+struct Item {
+  int64_t N = 0;
+  int r = 0, s = 0, leaf_max = 0, L = 0;
+  std::vector<int64_t> off, size;
+  std::vector<int64_t> oU, oV, oD, oWY, oWZ, oOm, oPs, oY, oZ;   // arena offsets by node id
+  const double *Om = nullptr, *Ps = nullptr, *Y = nullptr, *Z = nullptr;
+  int64_t node_rows(int64_t t) const { return level_of(t) == L ? size[t] : 2 * r; }
+  int level_of(int64_t t) const {
+    int l = 0;
+    while ((int64_t(2) << l) <= t) ++l;
+    return l;
+  }
+};
+
+struct Height {
+  std::vector<NodeTask> tasks;
+  NodeTask* d_tasks = nullptr;
+  int max_n = 0, max_r = 0, max_s = 0;
+};
+
+}  // namespace
+
+struct hbs_handle {
+  int precision = 0;
+  std::vector<Item> items;
+  double* arena = nullptr;
+  size_t arena_doubles = 0;
+  size_t factor_doubles = 0;
+  int* d_status = nullptr;
+  std::vector<Height> heights;
+  bool tasks_uploaded = false;
+  double* apply_ws = nullptr;
+  size_t apply_ws_doubles = 0;
+  GemmTask* d_gemm = nullptr;
+  size_t d_gemm_cap = 0;
+};
+
+namespace {
+
+int check_problem(const hbs_problem& p, int idx) {
+  if (p.N < 1 || p.r < 1 || p.s < 1 || p.leaf_max < 1)
+    return fail(HBS_ERR_ARG, "problem %d: N, r, s, leaf_max must be positive", idx);
+  if (!p.Omega || !p.Psi || !p.Y || !p.Z)
+    return fail(HBS_ERR_ARG, "problem %d: NULL input pointer", idx);
+  int L;
+  std::vector<int64_t> off, size;
+  build_tree(p.N, p.leaf_max, &L, &off, &size);
+  if (L == 0) {
+    if (p.N > p.s) return fail(HBS_ERR_SHAPE, "problem %d: single-node tree needs N <= s", idx);
+  } else {
+    int64_t mn = size[int64_t(1) << L], mx = mn;
+    for (int64_t t = int64_t(1) << L; t < (int64_t(2) << L); ++t) {
+      mn = std::min(mn, size[t]);
+      mx = std::max(mx, size[t]);
+    }
+    if (mn < p.r) return fail(HBS_ERR_SHAPE, "problem %d: a leaf has %lld < r rows", idx, (long long)mn);
+    if (mx + p.r > p.s)
+      return fail(HBS_ERR_SHAPE, "problem %d: leaf of %lld rows needs s >= leaf + r", idx, (long long)mx);
+    if (p.s < 3 * p.r) return fail(HBS_ERR_SHAPE, "problem %d: s < 3r", idx);
+  }
+  if (p.s > hbs::kMaxS)
+    return fail(HBS_ERR_UNSUPPORTED, "problem %d: s = %d exceeds %d", idx, p.s, hbs::kMaxS);
+  const int64_t nmax = (L == 0) ? p.N : std::max<int64_t>(2 * p.r, size[int64_t(1) << L]);
+  if (hbs::node_smem_doubles(int(nmax), p.r, p.s) * sizeof(double) > hbs::kMaxNodeSmemBytes)
+    return fail(HBS_ERR_UNSUPPORTED, "problem %d: node tile of %lld x %d exceeds shared memory",
+                idx, (long long)nmax, p.s);
+  return HBS_OK;
+}
+
+void build_tasks(hbs_handle* h) {
+  int maxL = 0;
+  for (auto& it : h->items) maxL = std::max(maxL, it.L);
+  h->heights.assign(maxL + 1, Height{});
+  for (auto& it : h->items) {
+    const int r = it.r, s = it.s;
+    for (int level = it.L; level >= 0; --level) {
+      Height& H = h->heights[it.L - level];
+      for (int64_t t = int64_t(1) << level; t < (int64_t(2) << level); ++t) {
+        NodeTask tk{};
+        const int64_t n = (it.L == 0) ? it.N : it.node_rows(t);
+        tk.n = int(n);
+        tk.r = r;
+        tk.s = s;
+        if (level == it.L) {
+          const int64_t o = it.off[t] * s;
+          tk.Om = it.Om + o;
+          tk.Ps = it.Ps + o;
+          tk.Y = it.Y + o;
+          tk.Z = it.Z + o;
+        } else {
+          tk.Om = h->arena + it.oOm[t];
+          tk.Ps = h->arena + it.oPs[t];
+          tk.Y = h->arena + it.oY[t];
+          tk.Z = h->arena + it.oZ[t];
+        }
+        tk.D = h->arena + it.oD[t];
+        if (level == 0) {
+          tk.is_root = 1;
+        } else {
+          tk.U = h->arena + it.oU[t];
+          tk.V = h->arena + it.oV[t];
+          tk.WY = h->arena + it.oWY[t];
+          tk.WZ = h->arena + it.oWZ[t];
+          const int64_t p = t / 2, row = (t % 2) * int64_t(r) * s;
+          tk.Om_p = h->arena + it.oOm[p] + row;
+          tk.Ps_p = h->arena + it.oPs[p] + row;
+          tk.Y_p = h->arena + it.oY[p] + row;
+          tk.Z_p = h->arena + it.oZ[p] + row;
+        }
+        H.tasks.push_back(tk);
+        H.max_n = std::max(H.max_n, tk.n);
+        H.max_r = std::max(H.max_r, r);
+        H.max_s = std::max(H.max_s, s);
+      }
+    }
+  }
+}
+
+int upload_tasks(hbs_handle* h, cudaStream_t st) {
+  for (auto& H : h->heights) {
+    if (!H.d_tasks) {
+      cudaError_t e = cudaMalloc(&H.d_tasks, H.tasks.size() * sizeof(NodeTask));
+      if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "task list: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMemcpyAsync(H.d_tasks, H.tasks.data(), H.tasks.size() * sizeof(NodeTask),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "task upload");
+  }
+  return HBS_OK;
+}
+
+void free_handle(hbs_handle* h) {
+  if (!h) return;
+  for (auto& H : h->heights) cudaFree(H.d_tasks);
+  cudaFree(h->arena);
+  cudaFree(h->d_status);
+  cudaFree(h->apply_ws);
+  cudaFree(h->d_gemm);
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hbs_last_error(void) { return g_last_error.c_str(); }
+
+int hbs_draw_gaussian(int64_t N, int32_t s, uint32_t stream_id, uint64_t seed, double* out,
+                      void* cuda_stream) {
+  if (!out || N < 1 || s < 1) return fail(HBS_ERR_ARG, "hbs_draw_gaussian: bad arguments");
+  cudaError_t e = hbs::launch_gaussian(N * int64_t(s), stream_id, seed, out,
+                                       static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "gaussian kernel");
+  return ok();
+}
+
+static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, const void* a,
+                          const void* b, const void* c, const void* d, const char* who) {
+  if (!op || !a || !b || !c || !d || s < 1 || op->N < 1)
+    return fail(HBS_ERR_ARG, "%s: bad arguments", who);
+  if (precision != HBS_PREC_FP64)
+    return fail(HBS_ERR_UNSUPPORTED, "%s: precision %d not built", who, precision);
+  if (!op->A && !op->fn) return fail(HBS_ERR_ARG, "%s: operator has neither A nor fn", who);
+  if (op->A && op->dtype != HBS_F64)
+    return fail(HBS_ERR_UNSUPPORTED, "%s: dense A must be FP64 in this build", who);
+  if (op->A && op->lda < op->N) return fail(HBS_ERR_ARG, "%s: lda < N", who);
+  return HBS_OK;
+}
+
+int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, const double* Omega,
+                        const double* Psi, double* Y, double* Z, void* cuda_stream) {
+  const int rc = check_operator(op, s, precision, Omega, Psi, Y, Z, "hbs_sample_products");
+  if (rc != HBS_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (op->A) {
+    cudaError_t e = hbs::launch_sample_dense_f64(static_cast<const double*>(op->A), op->lda,
+                                                 op->N, Omega, Psi, s, Y, Z, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sampling kernel");
+    return ok();
+  }
+  if (op->fn(op->user, 0, op->N, s, Omega, Y, cuda_stream) != 0)
+    return fail(HBS_ERR_CALLBACK, "callback failed for A");
+  if (op->fn(op->user, 1, op->N, s, Psi, Z, cuda_stream) != 0)
+    return fail(HBS_ERR_CALLBACK, "callback failed for A^*");
+  return ok();
+}
+
+int hbs_sample(const hbs_operator* op, int32_t s, uint64_t seed, int32_t precision,
+               double* Omega, double* Psi, double* Y, double* Z, void* cuda_stream) {
+  const int rc = check_operator(op, s, precision, Omega, Psi, Y, Z, "hbs_sample");
+  if (rc != HBS_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int64_t count = op->N * int64_t(s);
+  cudaError_t e = hbs::launch_gaussian(count, 0u, seed, Omega, st);
+  if (e == cudaSuccess) e = hbs::launch_gaussian(count, 1u, seed, Psi, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gaussian kernel");
+  return hbs_sample_products(op, s, precision, Omega, Psi, Y, Z, cuda_stream);
+}
+
+int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out) {
+  if (!out || !probs || batch < 1) return fail(HBS_ERR_ARG, "hbs_plan: bad arguments");
+  *out = nullptr;
+  if (precision != HBS_PREC_FP64)
+    return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: precision %d not built", precision);
+  for (int i = 0; i < batch; ++i) {
+    const int rc = check_problem(probs[i], i);
+    if (rc != HBS_OK) return rc;
+  }
+  auto* h = new hbs_handle();
+  h->precision = precision;
+  h->items.resize(batch);
+  size_t cursor = 0;
+  // factors
+  for (int i = 0; i < batch; ++i) {
+    Item& it = h->items[i];
+    const hbs_problem& p = probs[i];
+    it.N = p.N;
+    it.r = p.r;
+    it.s = p.s;
+    it.leaf_max = p.leaf_max;
+    build_tree(p.N, p.leaf_max, &it.L, &it.off, &it.size);
+    const int64_t count = int64_t(2) << it.L;
+    for (auto* v : {&it.oU, &it.oV, &it.oD, &it.oWY, &it.oWZ, &it.oOm, &it.oPs, &it.oY, &it.oZ})
+      v->assign(count, -1);
+    for (int64_t t = 1; t < count; ++t) {
+      const int64_t n = (it.L == 0) ? it.N : it.node_rows(t);
+      if (t > 1) {
+        it.oU[t] = int64_t(cursor);
+        cursor += size_t(n) * it.r;
+        it.oV[t] = int64_t(cursor);
+        cursor += size_t(n) * it.r;
+      }
+      it.oD[t] = int64_t(cursor);
+      cursor += size_t(n) * n;
+    }
+  }
+  h->factor_doubles = cursor;
+  // workspace and parent blocks
+  for (auto& it : h->items) {
+    const int64_t count = int64_t(2) << it.L;
+    for (int64_t t = 2; t < count; ++t) {
+      const int64_t n = it.node_rows(t);
+      it.oWY[t] = int64_t(cursor);
+      cursor += size_t(n) * n;
+      it.oWZ[t] = int64_t(cursor);
+      cursor += size_t(n) * n;
+    }
+    for (int64_t t = 1; t < (int64_t(1) << it.L); ++t) {
+      const size_t blk = size_t(2) * it.r * it.s;
+      for (auto* v : {&it.oOm, &it.oPs, &it.oY, &it.oZ}) {
+        (*v)[t] = int64_t(cursor);
+        cursor += blk;
+      }
+    }
+  }
+  h->arena_doubles = cursor;
+  cudaError_t e = cudaMalloc(&h->arena, std::max<size_t>(cursor, 1) * sizeof(double));
+  if (e != cudaSuccess) {
+    free_handle(h);
+    return fail(HBS_ERR_NOMEM, "arena of %zu bytes: %s", cursor * sizeof(double), cudaGetErrorString(e));
+  }
+  e = cudaMalloc(&h->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_handle(h);
+    return fail(HBS_ERR_NOMEM, "status word: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return ok();
+}
+
+int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream) {
+  if (!h || !probs) return fail(HBS_ERR_ARG, "hbs_execute: NULL argument");
+  bool changed = !h->tasks_uploaded;
+  for (size_t i = 0; i < h->items.size(); ++i) {
+    Item& it = h->items[i];
+    const hbs_problem& p = probs[i];
+    if (p.N != it.N || p.r != it.r || p.s != it.s || p.leaf_max != it.leaf_max)
+      return fail(HBS_ERR_ARG, "hbs_execute: problem %zu differs from the plan", i);
+    if (!p.Omega || !p.Psi || !p.Y || !p.Z)
+      return fail(HBS_ERR_ARG, "hbs_execute: problem %zu has a NULL input", i);
+    if (p.Omega != it.Om || p.Psi != it.Ps || p.Y != it.Y || p.Z != it.Z) changed = true;
+    it.Om = p.Omega;
+    it.Ps = p.Psi;
+    it.Y = p.Y;
+    it.Z = p.Z;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (changed) {
+    build_tasks(h);
+    const int rc = upload_tasks(h, st);
+    if (rc != HBS_OK) return rc;
+    h->tasks_uploaded = true;
+  }
+  for (auto& H : h->heights) {
+    cudaError_t e = hbs::launch_node_sweep_f64(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
+                                               H.max_s, h->d_status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
+  }
+  return ok();
+}
+
+int hbs_compress(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out,
+                 void* cuda_stream) {
+  int rc = hbs_plan(batch, probs, precision, out);
+  if (rc != HBS_OK) return rc;
+  rc = hbs_execute(*out, probs, cuda_stream);
+  if (rc != HBS_OK) {
+    free_handle(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int hbs_apply(hbs_handle* h, int32_t item, int trans, int32_t ncols, const double* X,
+              double* Out, void* cuda_stream) {
+  if (!h || !X || !Out || ncols < 1 || item < 0 || item >= int(h->items.size()))
+    return fail(HBS_ERR_ARG, "hbs_apply: bad arguments");
+  const Item& it = h->items[item];
+  const int r = it.r, c = ncols;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const double* A = h->arena;
+  // workspace: q-hat and u-hat for every node on levels 1..L, level-major, r x c per node
+  std::vector<int64_t> qoff(it.L + 1, 0), uoff(it.L + 1, 0);
+  size_t need = 0;
+  for (int l = 1; l <= it.L; ++l) {
+    qoff[l] = int64_t(need);
+    need += (size_t(1) << l) * r * c;
+  }
+  for (int l = 1; l <= it.L; ++l) {
+    uoff[l] = int64_t(need);
+    need += (size_t(1) << l) * r * c;
+  }
+  if (need > h->apply_ws_doubles) {
+    cudaFree(h->apply_ws);
+    h->apply_ws = nullptr;
+    h->apply_ws_doubles = 0;
+    cudaError_t e = cudaMalloc(&h->apply_ws, need * sizeof(double));
+    if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "apply workspace: %s", cudaGetErrorString(e));
+    h->apply_ws_doubles = need;
+  }
+  double* ws = h->apply_ws;
+  auto qhat = [&](int64_t t, int l) { return ws + qoff[l] + (t - (int64_t(1) << l)) * r * c; };
+  auto uhat = [&](int64_t t, int l) { return ws + uoff[l] + (t - (int64_t(1) << l)) * r * c; };
+  // bases: trans swaps U and V, and uses D^*
+  const std::vector<int64_t>& oIn = trans ? it.oU : it.oV;
+  const std::vector<int64_t>& oOut = trans ? it.oV : it.oU;
+  std::vector<std::vector<GemmTask>> passes;
+  if (it.L == 0) {
+    GemmTask g{};
+    g.A1 = A + it.oD[1]; g.lda1 = int(it.N); g.t1 = trans; g.k1 = int(it.N);
+    g.B1 = X; g.ldb1 = c; g.C = Out; g.ldc = c; g.m = int(it.N);
+    passes.push_back({g});
+  } else {
+    for (int l = it.L; l >= 1; --l) {                       // upward pass
+      std::vector<GemmTask> v;
+      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
+        GemmTask g{};
+        const int n = int(it.node_rows(t));
+        g.A1 = A + oIn[t]; g.lda1 = r; g.t1 = 1; g.k1 = n; g.m = r;
+        g.B1 = (l == it.L) ? X + it.off[t] * c : qhat(2 * t, l + 1);
+        g.ldb1 = c; g.C = qhat(t, l); g.ldc = c;
+        v.push_back(g);
+      }
+      passes.push_back(v);
+    }
+    for (int l = 0; l <= it.L; ++l) {                       // downward pass
+      std::vector<GemmTask> v;
+      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
+        GemmTask g{};
+        const int n = (l == 0) ? 2 * r : int(it.node_rows(t));
+        if (l == 0) {
+          g.A1 = A + it.oD[1]; g.lda1 = n; g.t1 = trans; g.k1 = n; g.m = n;
+          g.B1 = qhat(2, 1); g.ldb1 = c; g.C = uhat(2, 1); g.ldc = c;
+        } else {
+          g.A1 = A + oOut[t]; g.lda1 = r; g.t1 = 0; g.k1 = r; g.m = n;
+          g.B1 = uhat(t, l); g.ldb1 = c;
+          g.A2 = A + it.oD[t]; g.lda2 = n; g.t2 = trans; g.k2 = n;
+          if (l < it.L) {
+            g.B2 = qhat(2 * t, l + 1); g.ldb2 = c; g.C = uhat(2 * t, l + 1); g.ldc = c;
+          } else {
+            g.B2 = X + it.off[t] * c; g.ldb2 = c; g.C = Out + it.off[t] * c; g.ldc = c;
+          }
+        }
+        v.push_back(g);
+      }
+      passes.push_back(v);
+    }
+  }
+  size_t total = 0;
+  for (auto& p : passes) total += p.size();
+  if (total > h->d_gemm_cap) {
+    cudaFree(h->d_gemm);
+    h->d_gemm = nullptr;
+    h->d_gemm_cap = 0;
+    cudaError_t e = cudaMalloc(&h->d_gemm, total * sizeof(GemmTask));
+    if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "apply task list: %s", cudaGetErrorString(e));
+    h->d_gemm_cap = total;
+  }
+  std::vector<GemmTask> flat;
+  flat.reserve(total);
+  for (auto& p : passes) flat.insert(flat.end(), p.begin(), p.end());
+  cudaError_t e = cudaMemcpyAsync(h->d_gemm, flat.data(), total * sizeof(GemmTask),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "apply task upload");
+  size_t at = 0;
+  for (auto& p : passes) {
+    e = hbs::launch_gemm_tasks_f64(h->d_gemm + at, int(p.size()), c, st);
+    if (e != cudaSuccess) return cuda_fail(e, "apply kernel");
+    at += p.size();
+  }
+  return ok();
+}
+
+int hbs_sync_status(hbs_handle* h, void* cuda_stream) {
+  if (!h) return fail(HBS_ERR_ARG, "hbs_sync_status: NULL handle");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  int status = 0;
+  e = cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (status & hbs::kStatusNumeric)
+    return fail(HBS_ERR_NUMERIC, "zero or non-finite pivot in a triangular factor");
+  return ok();
+}
+
+void hbs_free(hbs_handle* h) { free_handle(h); }
+
+int hbs_tree_build(int64_t N, int32_t leaf_max, int32_t* L, int64_t* offsets, int64_t* sizes,
+                   int64_t max_nodes) {
+  if (N < 1 || leaf_max < 1 || !L) return fail(HBS_ERR_ARG, "hbs_tree_build: bad arguments");
+  int depth;
+  std::vector<int64_t> off, size;
+  build_tree(N, leaf_max, &depth, &off, &size);
+  *L = depth;
+  const int64_t count = (int64_t(2) << depth) - 1;
+  if (offsets || sizes) {
+    if (max_nodes < count) return fail(HBS_ERR_ARG, "hbs_tree_build: arrays hold %lld < %lld nodes",
+                                       (long long)max_nodes, (long long)count);
+    for (int64_t t = 1; t <= count; ++t) {
+      if (offsets) offsets[t - 1] = off[t];
+      if (sizes) sizes[t - 1] = size[t];
+    }
+  }
+  return ok();
+}
+
+int hbs_tree(const hbs_handle* h, int32_t item, int32_t* L, int64_t* offsets, int64_t* sizes) {
+  if (!h || !L || item < 0 || item >= int(h->items.size()))
+    return fail(HBS_ERR_ARG, "hbs_tree: bad arguments");
+  const Item& it = h->items[item];
+  *L = it.L;
+  const int64_t count = (int64_t(2) << it.L) - 1;
+  for (int64_t t = 1; t <= count; ++t) {
+    if (offsets) offsets[t - 1] = it.off[t];
+    if (sizes) sizes[t - 1] = it.size[t];
+  }
+  return ok();
+}
+
+int hbs_get_node(const hbs_handle* h, int32_t item, int64_t node, int32_t* n, double* U,
+                 double* V, double* D) {
+  if (!h || item < 0 || item >= int(h->items.size())) return fail(HBS_ERR_ARG, "hbs_get_node: bad item");
+  const Item& it = h->items[item];
+  if (node < 1 || node >= (int64_t(2) << it.L)) return fail(HBS_ERR_ARG, "hbs_get_node: bad node");
+  const int64_t rows = (it.L == 0) ? it.N : it.node_rows(node);
+  if (n) *n = int(rows);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && node > 1 && U)
+    e = cudaMemcpy(U, h->arena + it.oU[node], rows * it.r * sizeof(double), cudaMemcpyDefault);
+  if (e == cudaSuccess && node > 1 && V)
+    e = cudaMemcpy(V, h->arena + it.oV[node], rows * it.r * sizeof(double), cudaMemcpyDefault);
+  if (e == cudaSuccess && D)
+    e = cudaMemcpy(D, h->arena + it.oD[node], rows * rows * sizeof(double), cudaMemcpyDefault);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_get_node copy");
+  return ok();
+}
+
+size_t hbs_factor_bytes(const hbs_handle* h) { return h ? h->factor_doubles * sizeof(double) : 0; }
+
+int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream) {
+  if (!h || !dst) return fail(HBS_ERR_ARG, "hbs_copy_factors: bad arguments");
+  cudaError_t e = cudaMemcpyAsync(dst, h->arena, h->factor_doubles * sizeof(double),
+                                  cudaMemcpyDefault, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_copy_factors");
+  return ok();
+}
+
+}  // extern "C"

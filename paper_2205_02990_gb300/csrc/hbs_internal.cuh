@@ -1,0 +1,58 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace hbs {
+
+constexpr int kStatusNumeric = 1;   // bit set in the device status word on a bad pivot
+
+// One node of Algorithm 2 for the per-level sweep kernel. All matrices are row-major.
+struct NodeTask {
+  const double* Om;   // n x s test block Omega_tau   (leading dimension s)
+  const double* Ps;   // n x s test block Psi_tau
+  const double* Y;    // n x s sample block Y_tau
+  const double* Z;    // n x s sample block Z_tau
+  double* U;          // n x r output basis U_tau
+  double* V;          // n x r output basis V_tau
+  double* D;          // n x n output block D_tau
+  double* WY;         // n x n workspace: Y_tau Omega_tau^dagger
+  double* WZ;         // n x n workspace: Z_tau Psi_tau^dagger
+  double* Om_p;       // this node's r x s rows of the parent's blocks (leading dimension s):
+  double* Ps_p;       //   left child rows 0..r-1, right child rows r..2r-1; unused at the root
+  double* Y_p;
+  double* Z_p;
+  int32_t n, r, s;
+  int32_t is_root;    // 1: only D = Y_tau Omega_tau^dagger (root step of Algorithm 2)
+};
+
+// One small product task of Algorithm 1: C (m x ncols) = op1(A1) B1 [+ op2(A2) B2].
+// op(A) = A (A stored m x k, leading dimension lda) or A^T (A stored k x m, leading dim lda).
+struct GemmTask {
+  const double* A1; const double* B1;
+  const double* A2; const double* B2;   // A2 == NULL: single term
+  double* C;
+  int32_t m, k1, k2;
+  int32_t lda1, lda2;
+  int32_t ldb1, ldb2, ldc;
+  int32_t t1, t2;                       // 1 = transpose
+};
+
+// Shared-memory doubles for one node of n rows (sweep kernel).
+size_t node_smem_doubles(int n, int r, int s);
+constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
+constexpr int kMaxS = 192;              // register tile of the sample-row streaming
+
+cudaError_t launch_node_sweep_f64(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
+                                  int max_s, int* d_status, cudaStream_t st);
+cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, double* out,
+                            cudaStream_t st);
+cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,
+                                    const double* Ps, int s, double* Y, double* Z,
+                                    cudaStream_t st);
+cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st);
+
+}  // namespace hbs

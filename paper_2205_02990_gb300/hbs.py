@@ -1,0 +1,318 @@
+"""Thin Python binding of include/hbs.h (ctypes; argument marshalling only).
+
+Every computation runs in libhbs.so; this module only checks tensors, passes
+``tensor.data_ptr()`` and the current torch CUDA stream, and turns status codes into
+exceptions. Loading fails loudly when the library has not been built: there is no fallback.
+Function names follow the C ABI (``hbs_sample``, ``hbs_compress``, ``hbs_apply``, ``hbs_free``
+and the rest).
+"""
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libhbs.so")
+
+HBS_OK = 0
+HBS_ERR_ARG = -1
+HBS_ERR_SHAPE = -2
+HBS_ERR_NOMEM = -3
+HBS_ERR_CUDA = -4
+HBS_ERR_NUMERIC = -5
+HBS_ERR_TIMEOUT = -6
+HBS_ERR_CALLBACK = -7
+HBS_ERR_UNSUPPORTED = -8
+HBS_PREC_FP64 = 0
+HBS_F64 = 0
+HBS_F32 = 1
+
+EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan", "hbs_execute", "hbs_compress",
+            "hbs_apply", "hbs_sync_status", "hbs_free", "hbs_last_error", "hbs_tree",
+            "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors"]
+
+
+class HBSError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"hbs status {code}: {message}")
+        self.code = code
+
+
+MATMAT_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                             ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Operator(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("dtype", ctypes.c_int32), ("A", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("fn", MATMAT_FN), ("user", ctypes.c_void_p)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("r", ctypes.c_int32), ("s", ctypes.c_int32),
+                ("leaf_max", ctypes.c_int32), ("Omega", ctypes.c_void_p),
+                ("Psi", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("Z", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load():
+    """The loaded libhbs.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                           "`python -m paper_2205_02990_gb300.build`")
+    lib = ctypes.CDLL(_LIB_PATH)
+    c = ctypes
+    sig = {
+        "hbs_draw_gaussian": (c.c_int, [c.c_int64, c.c_int32, c.c_uint32, c.c_uint64, c.c_void_p, c.c_void_p]),
+        "hbs_sample": (c.c_int, [c.POINTER(_Operator), c.c_int32, c.c_uint64, c.c_int32, c.c_void_p,
+                                 c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "hbs_sample_products": (c.c_int, [c.POINTER(_Operator), c.c_int32, c.c_int32, c.c_void_p,
+                                          c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "hbs_plan": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p)]),
+        "hbs_execute": (c.c_int, [c.c_void_p, c.POINTER(_Problem), c.c_void_p]),
+        "hbs_compress": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p),
+                                   c.c_void_p]),
+        "hbs_apply": (c.c_int, [c.c_void_p, c.c_int32, c.c_int, c.c_int32, c.c_void_p, c.c_void_p,
+                                c.c_void_p]),
+        "hbs_sync_status": (c.c_int, [c.c_void_p, c.c_void_p]),
+        "hbs_free": (None, [c.c_void_p]),
+        "hbs_last_error": (c.c_char_p, []),
+        "hbs_tree": (c.c_int, [c.c_void_p, c.c_int32, c.POINTER(c.c_int32), c.c_void_p, c.c_void_p]),
+        "hbs_tree_build": (c.c_int, [c.c_int64, c.c_int32, c.POINTER(c.c_int32), c.c_void_p, c.c_void_p,
+                                     c.c_int64]),
+        "hbs_get_node": (c.c_int, [c.c_void_p, c.c_int32, c.c_int64, c.POINTER(c.c_int32), c.c_void_p,
+                                   c.c_void_p, c.c_void_p]),
+        "hbs_factor_bytes": (c.c_size_t, [c.c_void_p]),
+        "hbs_copy_factors": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != HBS_OK:
+        raise HBSError(code, load().hbs_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, shape=None, name="tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous (row-major)")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hbs_draw_gaussian(N, s, stream_id, seed, out):
+    """Fill ``out`` (N x s, float64, CUDA) from the counter-based generator."""
+    _check(load().hbs_draw_gaussian(N, s, stream_id, seed, _dev(out, (N, s), "out"), _stream()))
+
+
+def _operator(A, N):
+    """(ctypes operator, keep-alive) for a dense CUDA float64 tensor or a callable black box."""
+    if isinstance(A, torch.Tensor):
+        if (not A.is_cuda or A.dtype != torch.float64 or A.dim() != 2 or A.shape[0] != A.shape[1]
+                or A.stride(1) != 1 or A.stride(0) < A.shape[0]):
+            raise TypeError("A must be a square row-major CUDA float64 matrix")
+        N = A.shape[0]
+        op = _Operator(N=N, dtype=HBS_F64, A=A.data_ptr(), lda=A.stride(0), fn=MATMAT_FN(), user=None)
+        return op, None, N
+    if N is None:
+        raise ValueError("N is required with a callable operator")
+
+    def trampoline(user, trans, n, ncols, X, Out, stream):
+        try:
+            A(int(trans), _wrap(X, n, ncols), _wrap(Out, n, ncols))
+            return 0
+        except Exception:            # reported to the caller as HBS_ERR_CALLBACK
+            return 1
+
+    keep = MATMAT_FN(trampoline)
+    return _Operator(N=N, dtype=HBS_F64, A=None, lda=0, fn=keep, user=None), keep, N
+
+
+def hbs_sample(A, s, seed, Omega, Psi, Y, Z, precision=HBS_PREC_FP64, N=None):
+    """Draw Omega, Psi and form Y = A Omega, Z = A^* Psi.
+
+    ``A`` is a dense CUDA float64 tensor (N x N, row-major) or a callable
+    ``fn(trans, X, Out)`` that writes A X (trans = 0) or A^* X (trans = 1) into ``Out``
+    (both N x s CUDA float64 tensors) on the current stream.
+    """
+    op, keep, N = _operator(A, N)
+    ptrs = [_dev(x, (N, s), nm) for x, nm in ((Omega, "Omega"), (Psi, "Psi"), (Y, "Y"), (Z, "Z"))]
+    _check(load().hbs_sample(ctypes.byref(op), s, seed, precision, *ptrs, _stream()))
+    del keep
+
+
+def hbs_sample_products(A, s, Omega, Psi, Y, Z, precision=HBS_PREC_FP64, N=None):
+    """Y = A Omega, Z = A^* Psi for test matrices already drawn (same operator rules)."""
+    op, keep, N = _operator(A, N)
+    ptrs = [_dev(x, (N, s), nm) for x, nm in ((Omega, "Omega"), (Psi, "Psi"), (Y, "Y"), (Z, "Z"))]
+    _check(load().hbs_sample_products(ctypes.byref(op), s, precision, *ptrs, _stream()))
+    del keep
+
+
+class _CudaView:
+    """A device buffer described by __cuda_array_interface__ (viewed by torch without a copy)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _wrap(ptr, n, ncols):
+    return torch.as_tensor(_CudaView(ptr, (n, ncols)), device="cuda")
+
+
+@dataclass
+class Problem:
+    """One compression problem: test matrices and samples (N x s CUDA float64 tensors)."""
+    N: int
+    r: int
+    s: int
+    leaf_max: int
+    Omega: torch.Tensor
+    Psi: torch.Tensor
+    Y: torch.Tensor
+    Z: torch.Tensor
+
+    def _c(self):
+        sh = (self.N, self.s)
+        return _Problem(N=self.N, r=self.r, s=self.s, leaf_max=self.leaf_max,
+                        Omega=_dev(self.Omega, sh, "Omega").value, Psi=_dev(self.Psi, sh, "Psi").value,
+                        Y=_dev(self.Y, sh, "Y").value, Z=_dev(self.Z, sh, "Z").value)
+
+
+def _problems(problems):
+    arr = (_Problem * len(problems))(*[p._c() for p in problems])
+    return arr
+
+
+class Handle:
+    """Owns an hbs_handle (factors + workspace); freed by ``hbs_free`` or on deletion."""
+
+    def __init__(self, ptr, problems):
+        self._ptr = ptr
+        self.problems = list(problems)
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle already freed")
+        return self._ptr
+
+    def free(self):
+        if self._ptr:
+            load().hbs_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def hbs_plan(problems, precision=HBS_PREC_FP64):
+    h = ctypes.c_void_p()
+    arr = _problems(problems)
+    _check(load().hbs_plan(len(problems), arr, precision, ctypes.byref(h)))
+    return Handle(h, problems)
+
+
+def hbs_execute(handle, problems=None):
+    problems = handle.problems if problems is None else list(problems)
+    _check(load().hbs_execute(handle.ptr, _problems(problems), _stream()))
+    handle.problems = problems
+
+
+def hbs_compress(problems, precision=HBS_PREC_FP64):
+    """Plan and run Algorithm 2 for a batch of problems; returns a Handle."""
+    h = ctypes.c_void_p()
+    arr = _problems(problems)
+    _check(load().hbs_compress(len(problems), arr, precision, ctypes.byref(h), _stream()))
+    return Handle(h, problems)
+
+
+def hbs_apply(handle, X, Out, item=0, trans=False):
+    """Out = A~ X (or A~^* X) by Algorithm 1; X, Out N x c CUDA float64."""
+    N = handle.problems[item].N
+    if X.dim() != 2:
+        raise ValueError("X must be 2-D (N x c)")
+    c = X.shape[1]
+    _check(load().hbs_apply(handle.ptr, item, int(bool(trans)), c, _dev(X, (N, c), "X"),
+                            _dev(Out, (N, c), "Out"), _stream()))
+
+
+def hbs_sync_status(handle):
+    _check(load().hbs_sync_status(handle.ptr, _stream()))
+
+
+def hbs_free(handle):
+    handle.free()
+
+
+def hbs_tree_build(N, leaf_max):
+    """(L, offsets, sizes) of the Section 3.1 tree, node ids 1.. at index 0.."""
+    lib = load()
+    L = ctypes.c_int32()
+    _check(lib.hbs_tree_build(N, leaf_max, ctypes.byref(L), None, None, 0))
+    count = (2 << L.value) - 1
+    off = (ctypes.c_int64 * count)()
+    size = (ctypes.c_int64 * count)()
+    _check(lib.hbs_tree_build(N, leaf_max, ctypes.byref(L), off, size, count))
+    return L.value, list(off), list(size)
+
+
+def hbs_tree(handle, item=0):
+    lib = load()
+    L = ctypes.c_int32()
+    _check(lib.hbs_tree(handle.ptr, item, ctypes.byref(L), None, None))
+    count = (2 << L.value) - 1
+    off = (ctypes.c_int64 * count)()
+    size = (ctypes.c_int64 * count)()
+    _check(lib.hbs_tree(handle.ptr, item, ctypes.byref(L), off, size))
+    return L.value, list(off), list(size)
+
+
+def hbs_get_node(handle, node, item=0):
+    """(U, V, D) of a node as float64 CPU tensors (U, V are None for the root)."""
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib.hbs_get_node(handle.ptr, item, node, ctypes.byref(n), None, None, None))
+    r = handle.problems[item].r
+    D = torch.empty((n.value, n.value), dtype=torch.float64)
+    if node == 1:
+        _check(lib.hbs_get_node(handle.ptr, item, node, ctypes.byref(n), None, None,
+                                ctypes.c_void_p(D.data_ptr())))
+        return None, None, D
+    U = torch.empty((n.value, r), dtype=torch.float64)
+    V = torch.empty((n.value, r), dtype=torch.float64)
+    _check(lib.hbs_get_node(handle.ptr, item, node, ctypes.byref(n), ctypes.c_void_p(U.data_ptr()),
+                            ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(D.data_ptr())))
+    return U, V, D
+
+
+def hbs_factor_bytes(handle):
+    return int(load().hbs_factor_bytes(handle.ptr))
+
+
+def hbs_copy_factors(handle, dst):
+    """Asynchronous copy of every factor into ``dst`` (uint8/float64 tensor, host or device)."""
+    if dst.numel() * dst.element_size() < hbs_factor_bytes(handle):
+        raise ValueError("destination too small")
+    _check(load().hbs_copy_factors(handle.ptr, ctypes.c_void_p(dst.data_ptr()), _stream()))

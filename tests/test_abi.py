@@ -1,0 +1,93 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the header declares,
+builds the Section 3.1 tree exactly like the oracle, and rejects bad arguments and shapes on the
+host before touching the device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+from oracle.tree import build_tree
+
+pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_02990_gb300 import hbs
+    if not os.path.exists(hbs._LIB_PATH):
+        from paper_2205_02990_gb300.build import build
+        build()
+    return hbs.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hbs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(hbs_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(n for n in names if n not in ("hbs_matmat_fn",)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2205_02990_gb300 import hbs
+    assert sorted(hbs.EXPORTED) == names
+
+
+@pytest.mark.parametrize("N,leaf", [(400, 100), (1, 1), (1000, 16), (1023, 64), (32768, 64),
+                                    (97, 10), (5, 7), (4097, 3)])
+def test_tree_bit_exact_with_oracle(lib, N, leaf):
+    from paper_2205_02990_gb300 import hbs_tree_build
+    L, off, size = hbs_tree_build(N, leaf)
+    Lo, offo, sizeo = build_tree(N, leaf)
+    assert L == Lo
+    assert off == offo[1:] and size == sizeo[1:]
+
+
+def _problem(N, r, s, leaf, ptr=0x1000):
+    from paper_2205_02990_gb300.hbs import _Problem
+    return _Problem(N=N, r=r, s=s, leaf_max=leaf, Omega=ptr, Psi=ptr, Y=ptr, Z=ptr)
+
+
+@pytest.mark.parametrize("N,r,s,leaf,code", [
+    (1024, 10, 30, 64, -2),      # leaf 64 > s - r: no leaf nullspace (configs as written)
+    (1024, 10, 25, 16, -2),      # s < 3r
+    (100, 10, 30, 8, -2),        # leaves of 6-7 rows < r
+    (40, 3, 30, 64, -2),         # single node with N > s
+    (0, 3, 30, 64, -1),          # empty problem
+    (100, 0, 30, 64, -1),
+    (100, 4, 0, 64, -1),
+    (100, 4, 12, 0, -1),
+    (4096, 64, 200, 128, -8),    # s beyond the register tile of this build
+])
+def test_plan_rejects_on_host(lib, N, r, s, leaf, code):
+    arr = (type(_problem(1, 1, 1, 1)) * 1)(_problem(N, r, s, leaf))
+    h = ctypes.c_void_p()
+    rc = lib.hbs_plan(1, arr, 0, ctypes.byref(h))
+    assert rc == code
+    assert not h.value
+    assert len(lib.hbs_last_error()) > 0
+
+
+def test_null_arguments_rejected(lib):
+    h = ctypes.c_void_p()
+    assert lib.hbs_plan(1, None, 0, ctypes.byref(h)) == -1
+    arr = (type(_problem(1, 1, 1, 1)) * 1)(_problem(1024, 10, 30, 16, ptr=0))
+    assert lib.hbs_plan(1, arr, 0, ctypes.byref(h)) == -1
+    assert lib.hbs_plan(1, arr, 7, ctypes.byref(h)) in (-1, -8)
+    assert lib.hbs_draw_gaussian(0, 3, 0, 1, None, None) == -1
+    assert lib.hbs_apply(None, 0, 0, 1, None, None, None) == -1
+    assert lib.hbs_sync_status(None, None) == -1
+    lib.hbs_free(None)                                   # NULL-safe
+    assert lib.hbs_tree_build(0, 4, ctypes.byref(ctypes.c_int32()), None, None, 0) == -1
+
+
+def test_unsupported_precision(lib):
+    arr = (type(_problem(1, 1, 1, 1)) * 1)(_problem(1024, 10, 30, 16))
+    h = ctypes.c_void_p()
+    assert lib.hbs_plan(1, arr, 5, ctypes.byref(h)) == -8
