@@ -183,6 +183,37 @@ int hbs_get_node(const hbs_handle* h, int32_t item, int64_t node, int32_t* n, do
 size_t hbs_factor_bytes(const hbs_handle* h);
 int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Apply without allocating (no counterpart in the paper; a service of this library).
+ *
+ * hbs_apply grows a device workspace with cudaMalloc the first time it needs more. Some callers
+ * must not allocate: cudaMalloc synchronizes the whole device and fails when another allocator
+ * (for instance a framework's caching pool) already holds the GPU's memory, which latency-bound
+ * services and black-box operator callbacks (hbs_matmat_fn) that apply a compressed matrix in
+ * the middle of someone else's stream cannot accept. hbs_apply_static computes exactly what
+ * hbs_apply computes (Algorithm 1, same kernel) but keeps its workspace and its work list in
+ * fixed arrays inside the library (file-scope device memory, reserved on every GPU that loads
+ * the library until the process exits), so it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * Limits: the workspace of one call, 2 (2^(L+1) - 2) r ncols doubles, must not exceed
+ * HBS_APPLY_STATIC_MAX_DOUBLES, and the work list, 2^(L+2) - 3 node products (2^(L+1) - 1 when
+ * L = 0), must not exceed HBS_APPLY_STATIC_MAX_TASKS; larger requests return
+ * HBS_ERR_UNSUPPORTED with the limit in the message, before anything is queued.
+ *
+ * The first call on each device looks up the device addresses of the two arrays
+ * (cudaGetSymbolAddress, with that device current) and checks the result; make that first call
+ * before any stream capture. Every call on a device shares the same two arrays and they keep
+ * the last call's contents (nothing in them needs to start at zero: every entry a call reads
+ * it has written first). Calls whose GPU work overlaps in time -- on different streams, or from
+ * several threads -- race on the arrays; queue them on one stream or order them yourself.
+ * Arguments and errors otherwise as hbs_apply.
+ */
+#define HBS_APPLY_STATIC_MAX_DOUBLES 2097152   /* 16 MiB of FP64 workspace per device */
+#define HBS_APPLY_STATIC_MAX_TASKS 16384      /* 1.25 MiB of work list per device */
+int hbs_apply_static(const hbs_handle* h, int32_t item, int trans, int32_t ncols,
+                     const double* X, double* Out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

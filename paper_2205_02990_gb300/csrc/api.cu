@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -558,3 +559,133 @@ int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream) {
 }
 
 }  // extern "C"
+
+// ---- hbs_apply_static: Algorithm 1 with workspace and work list in fixed device arrays -----
+
+namespace {
+
+// Reserved on every GPU that loads the library, until exit. Host code may not take these
+// names as device addresses: the per-device addresses come from cudaGetSymbolAddress below.
+static __device__ __align__(256) double g_static_apply_ws[HBS_APPLY_STATIC_MAX_DOUBLES];
+static __device__ __align__(256) GemmTask g_static_apply_tasks[HBS_APPLY_STATIC_MAX_TASKS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double* g_static_ws_ptr[kMaxDevices] = {};
+GemmTask* g_static_task_ptr[kMaxDevices] = {};
+
+// Device addresses of the two arrays on the current device (looked up once per device).
+int static_arrays(double** ws, GemmTask** tasks) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(HBS_ERR_UNSUPPORTED, "hbs_apply_static: device %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ws_ptr[dev]) {
+    void* a = nullptr;
+    void* b = nullptr;
+    e = cudaGetSymbolAddress(&a, g_static_apply_ws);
+    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetSymbolAddress(workspace)");
+    e = cudaGetSymbolAddress(&b, g_static_apply_tasks);
+    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetSymbolAddress(work list)");
+    g_static_task_ptr[dev] = static_cast<GemmTask*>(b);
+    g_static_ws_ptr[dev] = static_cast<double*>(a);
+  }
+  *ws = g_static_ws_ptr[dev];
+  *tasks = g_static_task_ptr[dev];
+  return HBS_OK;
+}
+
+}  // namespace
+
+extern "C" int hbs_apply_static(const hbs_handle* h, int32_t item, int trans, int32_t ncols,
+                                const double* X, double* Out, void* cuda_stream) {
+  if (!h || !X || !Out || ncols < 1 || item < 0 || item >= int(h->items.size()))
+    return fail(HBS_ERR_ARG, "hbs_apply_static: bad arguments");
+  const Item& it = h->items[item];
+  const int r = it.r, c = ncols;
+  // size checks first: nothing is queued for a request beyond the fixed arrays
+  std::vector<int64_t> qoff(it.L + 1, 0), uoff(it.L + 1, 0);
+  size_t need = 0;
+  for (int l = 1; l <= it.L; ++l) {
+    qoff[l] = int64_t(need);
+    need += (size_t(1) << l) * r * c;
+  }
+  for (int l = 1; l <= it.L; ++l) {
+    uoff[l] = int64_t(need);
+    need += (size_t(1) << l) * r * c;
+  }
+  const size_t ntasks = (it.L == 0) ? 1 : (size_t(4) << it.L) - 3;
+  if (need > size_t(HBS_APPLY_STATIC_MAX_DOUBLES))
+    return fail(HBS_ERR_UNSUPPORTED,
+                "hbs_apply_static: workspace of %zu doubles exceeds the fixed %d (L=%d, r=%d, ncols=%d)",
+                need, HBS_APPLY_STATIC_MAX_DOUBLES, it.L, r, c);
+  if (ntasks > size_t(HBS_APPLY_STATIC_MAX_TASKS))
+    return fail(HBS_ERR_UNSUPPORTED, "hbs_apply_static: %zu node products exceed the fixed %d (L=%d)",
+                ntasks, HBS_APPLY_STATIC_MAX_TASKS, it.L);
+  double* ws = nullptr;
+  GemmTask* d_tasks = nullptr;
+  const int rc = static_arrays(&ws, &d_tasks);
+  if (rc != HBS_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const double* A = h->arena;
+  auto qhat = [&](int64_t t, int l) { return ws + qoff[l] + (t - (int64_t(1) << l)) * r * c; };
+  auto uhat = [&](int64_t t, int l) { return ws + uoff[l] + (t - (int64_t(1) << l)) * r * c; };
+  const std::vector<int64_t>& oIn = trans ? it.oU : it.oV;
+  const std::vector<int64_t>& oOut = trans ? it.oV : it.oU;
+  std::vector<GemmTask> flat;
+  std::vector<int> pass_sizes;
+  flat.reserve(ntasks);
+  if (it.L == 0) {
+    GemmTask g{};
+    g.A1 = A + it.oD[1]; g.lda1 = int(it.N); g.t1 = trans; g.k1 = int(it.N);
+    g.B1 = X; g.ldb1 = c; g.C = Out; g.ldc = c; g.m = int(it.N);
+    flat.push_back(g);
+    pass_sizes.push_back(1);
+  } else {
+    for (int l = it.L; l >= 1; --l) {                       // upward pass
+      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
+        GemmTask g{};
+        const int n = int(it.node_rows(t));
+        g.A1 = A + oIn[t]; g.lda1 = r; g.t1 = 1; g.k1 = n; g.m = r;
+        g.B1 = (l == it.L) ? X + it.off[t] * c : qhat(2 * t, l + 1);
+        g.ldb1 = c; g.C = qhat(t, l); g.ldc = c;
+        flat.push_back(g);
+      }
+      pass_sizes.push_back(1 << l);
+    }
+    for (int l = 0; l <= it.L; ++l) {                       // downward pass
+      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
+        GemmTask g{};
+        const int n = (l == 0) ? 2 * r : int(it.node_rows(t));
+        if (l == 0) {
+          g.A1 = A + it.oD[1]; g.lda1 = n; g.t1 = trans; g.k1 = n; g.m = n;
+          g.B1 = qhat(2, 1); g.ldb1 = c; g.C = uhat(2, 1); g.ldc = c;
+        } else {
+          g.A1 = A + oOut[t]; g.lda1 = r; g.t1 = 0; g.k1 = r; g.m = n;
+          g.B1 = uhat(t, l); g.ldb1 = c;
+          g.A2 = A + it.oD[t]; g.lda2 = n; g.t2 = trans; g.k2 = n;
+          if (l < it.L) {
+            g.B2 = qhat(2 * t, l + 1); g.ldb2 = c; g.C = uhat(2 * t, l + 1); g.ldc = c;
+          } else {
+            g.B2 = X + it.off[t] * c; g.ldb2 = c; g.C = Out + it.off[t] * c; g.ldc = c;
+          }
+        }
+        flat.push_back(g);
+      }
+      pass_sizes.push_back(1 << l);
+    }
+  }
+  // pageable source: the copy is staged before this call returns, nothing is allocated here
+  cudaError_t e = cudaMemcpyAsync(d_tasks, flat.data(), flat.size() * sizeof(GemmTask),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: work list upload");
+  size_t at = 0;
+  for (int cnt : pass_sizes) {
+    e = hbs::launch_gemm_tasks_f64(d_tasks + at, cnt, c, st);
+    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: apply kernel");
+    at += size_t(cnt);
+  }
+  return ok();
+}

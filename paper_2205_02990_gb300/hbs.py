@@ -30,7 +30,8 @@ HBS_F32 = 1
 
 EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan", "hbs_execute", "hbs_compress",
             "hbs_apply", "hbs_sync_status", "hbs_free", "hbs_last_error", "hbs_tree",
-            "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors"]
+            "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
+            "hbs_apply_static"]
 
 
 class HBSError(RuntimeError):
@@ -89,6 +90,8 @@ def load():
                                    c.c_void_p, c.c_void_p]),
         "hbs_factor_bytes": (c.c_size_t, [c.c_void_p]),
         "hbs_copy_factors": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
+        "hbs_apply_static": (c.c_int, [c.c_void_p, c.c_int32, c.c_int, c.c_int32, c.c_void_p,
+                                       c.c_void_p, c.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -256,6 +259,17 @@ def hbs_apply(handle, X, Out, item=0, trans=False):
     c = X.shape[1]
     _check(load().hbs_apply(handle.ptr, item, int(bool(trans)), c, _dev(X, (N, c), "X"),
                             _dev(Out, (N, c), "Out"), _stream()))
+
+
+def hbs_apply_static(handle, X, Out, item=0, trans=False):
+    """As ``hbs_apply``, but allocating nothing: the workspace and work list live in fixed
+    device arrays inside the library (see the limits and sharing rules in include/hbs.h)."""
+    N = handle.problems[item].N
+    if X.dim() != 2:
+        raise ValueError("X must be 2-D (N x c)")
+    c = X.shape[1]
+    _check(load().hbs_apply_static(handle.ptr, item, int(bool(trans)), c, _dev(X, (N, c), "X"),
+                                   _dev(Out, (N, c), "Out"), _stream()))
 
 
 def hbs_sync_status(handle):
