@@ -47,7 +47,11 @@ typedef enum {
 } hbs_status;
 
 typedef enum {
-  HBS_PREC_FP64 = 0         /* every step in IEEE binary64 on the FP64 pipe */
+  HBS_PREC_FP64 = 0,        /* every step in IEEE binary64 on the FP64 pipe */
+  HBS_PREC_MIXED_BF16X3 = 1,/* sampling: FP32 A and FP64 Omega split into 2 bfloat16 slices,
+                               3 slice products on the tensor cores, FP32 accumulation over
+                               chunks of 2048, chunks summed in FP64 (~16 significant bits) */
+  HBS_PREC_MIXED_BF16X6 = 2 /* as above with 3 slices and 6 products (~24 significant bits) */
 } hbs_precision;
 
 typedef enum { HBS_F64 = 0, HBS_F32 = 1 } hbs_dtype;
@@ -86,6 +90,10 @@ typedef struct {
   void* user;
 } hbs_operator;
 
+/* Precision of the products (hbs_sample, hbs_sample_products): HBS_PREC_FP64 needs a dense A in
+ * HBS_F64 or a callback; the mixed precisions need a dense A in HBS_F32 with lda a multiple of
+ * 4 and s <= 256, and keep Omega, Psi, Y, Z in FP64. */
+
 /* Randomized samples (Algorithm 2, first block): draws Omega (stream 0) and Psi (stream 1)
  * from `seed` as hbs_draw_gaussian does, then Y = A Omega and Z = A^* Psi.
  * Omega, Psi, Y, Z: device, FP64, row-major N x s (leading dimension s), written.
@@ -99,6 +107,11 @@ int hbs_sample(const hbs_operator* op, int32_t s, uint64_t seed, int32_t precisi
  * N x s. Same operator rules and errors as hbs_sample. */
 int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, const double* Omega,
                         const double* Psi, double* Y, double* Z, void* cuda_stream);
+
+/* Waits for `cuda_stream` and returns the device status of the tensor-core sampling on the
+ * current device since the last call: HBS_OK, or HBS_ERR_TIMEOUT if a bounded wait inside the
+ * kernel gave up (the products are then invalid). Clears the status. */
+int hbs_sample_sync(void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------------
  * One compression problem: test matrices and samples of one N x N matrix.

@@ -10,6 +10,7 @@
 // Work lists: height t = L_i - level groups level L_i - t of every item, so one launch per
 // height covers a whole batch of trees of different depths; heights run finest first.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -228,12 +229,20 @@ static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, 
                           const void* b, const void* c, const void* d, const char* who) {
   if (!op || !a || !b || !c || !d || s < 1 || op->N < 1)
     return fail(HBS_ERR_ARG, "%s: bad arguments", who);
-  if (precision != HBS_PREC_FP64)
-    return fail(HBS_ERR_UNSUPPORTED, "%s: precision %d not built", who, precision);
+  if (precision != HBS_PREC_FP64 && precision != HBS_PREC_MIXED_BF16X3 &&
+      precision != HBS_PREC_MIXED_BF16X6)
+    return fail(HBS_ERR_ARG, "%s: unknown precision %d", who, precision);
   if (!op->A && !op->fn) return fail(HBS_ERR_ARG, "%s: operator has neither A nor fn", who);
-  if (op->A && op->dtype != HBS_F64)
-    return fail(HBS_ERR_UNSUPPORTED, "%s: dense A must be FP64 in this build", who);
   if (op->A && op->lda < op->N) return fail(HBS_ERR_ARG, "%s: lda < N", who);
+  if (precision == HBS_PREC_FP64) {
+    if (op->A && op->dtype != HBS_F64)
+      return fail(HBS_ERR_UNSUPPORTED, "%s: FP64 products need a FP64 dense A", who);
+  } else {
+    if (!op->A || op->dtype != HBS_F32)
+      return fail(HBS_ERR_UNSUPPORTED, "%s: mixed products need a dense FP32 A", who);
+    if (op->lda % 4 != 0 || s > 256 || op->N > (int64_t(1) << 30))
+      return fail(HBS_ERR_UNSUPPORTED, "%s: mixed products need lda %% 4 == 0 and s <= 256", who);
+  }
   return HBS_OK;
 }
 
@@ -242,6 +251,19 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
   const int rc = check_operator(op, s, precision, Omega, Psi, Y, Z, "hbs_sample_products");
   if (rc != HBS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (precision != HBS_PREC_FP64) {
+    static const int kchunk = [] {                 // tuning override; 0 = split for occupancy
+      const char* v = getenv("HBS_TC_KCHUNK");
+      const int k = v ? atoi(v) : 0;
+      return (k >= 64 && k % 64 == 0) ? k : 0;
+    }();
+    cudaError_t e = hbs::launch_sample_dense_tc(static_cast<const float*>(op->A), op->lda, op->N,
+                                                Omega, Psi, s, Y, Z,
+                                                precision == HBS_PREC_MIXED_BF16X3 ? 2 : 3,
+                                                kchunk, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core sampling");
+    return ok();
+  }
   if (op->A) {
     cudaError_t e = hbs::launch_sample_dense_f64(static_cast<const double*>(op->A), op->lda,
                                                  op->N, Omega, Psi, s, Y, Z, st);
@@ -252,6 +274,17 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
     return fail(HBS_ERR_CALLBACK, "callback failed for A");
   if (op->fn(op->user, 1, op->N, s, Psi, Z, cuda_stream) != 0)
     return fail(HBS_ERR_CALLBACK, "callback failed for A^*");
+  return ok();
+}
+
+int hbs_sample_sync(void* cuda_stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  int status = 0;
+  e = hbs::sample_tc_status(&status, true);
+  if (e != cudaSuccess) return cuda_fail(e, "sampling status read");
+  if (status & hbs::kStatusTimeout)
+    return fail(HBS_ERR_TIMEOUT, "tensor-core sampling: a bounded device wait gave up");
   return ok();
 }
 
@@ -271,7 +304,7 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
   if (!out || !probs || batch < 1) return fail(HBS_ERR_ARG, "hbs_plan: bad arguments");
   *out = nullptr;
   if (precision != HBS_PREC_FP64)
-    return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: precision %d not built", precision);
+    return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: sweep precision %d not built", precision);
   for (int i = 0; i < batch; ++i) {
     const int rc = check_problem(probs[i], i);
     if (rc != HBS_OK) return rc;

@@ -9,6 +9,7 @@
 namespace hbs {
 
 constexpr int kStatusNumeric = 1;   // bit set in the device status word on a bad pivot
+constexpr int kStatusTimeout = 2;   // bit set when a bounded device-side wait gave up
 
 // One node of Algorithm 2 for the per-level sweep kernel. All matrices are row-major.
 struct NodeTask {
@@ -53,6 +54,13 @@ cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, do
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,
                                     const double* Ps, int s, double* Y, double* Z,
                                     cudaStream_t st);
+// Tensor-core sampling (sample_tc.cu): A FP32 row-major (lda % 4 == 0), slices = 2 (bf16x3) or
+// 3 (bf16x6), s <= 256; kchunk = reduction columns per split (0: chosen to fill the GPU). The
+// scratch it grows holds the device status word at its start.
+cudaError_t launch_sample_dense_tc(const float* A, int64_t lda, int64_t N, const double* Om,
+                                   const double* Ps, int s, double* Y, double* Z, int slices,
+                                   int kchunk, cudaStream_t st);
+cudaError_t sample_tc_status(int* host_status, bool clear);
 cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st);
 
 }  // namespace hbs

@@ -1,0 +1,690 @@
+// Mixed-precision sampling Y = A Omega, Z = A^* Psi (Algorithm 2, first block) on the
+// 5th-generation tensor cores (tcgen05, sm_103a) with split-BF16 compensated products.
+//
+// A is FP32 (row-major N x N). Each FP32 value a is split into P bfloat16 slices by repeated
+// round-to-nearest (a = a_0 + a_1 + ... up to the last slice's rounding), each FP64 entry of
+// Omega/Psi into Q slices the same way. C = sum over slice pairs (p, q) with p + q < max(P, Q)
+// of A_p B_q^*: P = Q = 2 gives 3 products ("bf16x3", ~16 significant bits), P = Q = 3 gives 6
+// ("bf16x6", ~24 bits).
+//
+// Accumulation. The tensor core adds each MMA result into its FP32 accumulator with a
+// truncating rounding, so an accumulator that collects many MMAs drifts by ~0.5 ulp per MMA
+// (measured: relative error growing linearly with the reduction length). Here an accumulator
+// collects only the MMAs of DR reduction steps of 64 columns: the small slice products first,
+// the leading pair (0, 0) last, so only the last few MMAs truncate at full magnitude. It is
+// then drained into a double-float (hi + lo, TwoSum in FP32) running sum kept in tensor
+// memory, while the tensor core fills the other accumulator of a ping-pong pair. The running
+// sum goes out as FP64; reduction splits exist only to balance the grid and are summed in FP64.
+//
+// CTA (320 threads, one per SM): warp 0 issues TMA loads (the FP32 A tile, unswizzled, and the
+// Q pre-split B tiles, 128-byte swizzled); warp 1 owns the tensor memory and one thread issues
+// tcgen05.mma (M = 128, N = BN <= 128, K = 16 per instruction); warps 2-5 split the FP32 A tile
+// into P bf16 tiles written in the 128-byte-swizzled K-major layout the MMA reads (transposing
+// it on the way for Z = A^* Psi); warps 6-9 drain the accumulators (tcgen05.ld / tcgen05.st)
+// and write the result. Tensor memory: two accumulators, hi, lo (4 x 128 columns).
+// mbarriers hand buffers between the roles; every wait is bounded in time and sets the
+// timeout bit of the status word instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <vector>
+
+#include "hbs_internal.cuh"
+
+namespace hbs {
+namespace {
+
+constexpr int kTcThreads = 320;
+constexpr int BM = 128;                       // MMA M: rows of C per CTA
+constexpr int BK = 64;                        // reduction columns per stage (128 B of bf16)
+constexpr int kStageABytes = BM * BK * 4;     // FP32 A tile
+constexpr int kSliceABytes = BM * BK * 2;     // one bf16 slice of the A tile
+constexpr unsigned long long kWaitNs = 500000000ull;   // 0.5 s per wait, then give up
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ bool aborted(const int* status) {
+  return (*reinterpret_cast<const volatile int*>(status) & kStatusTimeout) != 0;
+}
+
+// Wait for the phase with the given parity; false (and the timeout bit set) after kWaitNs, or,
+// when `abortable`, as soon as another CTA of the grid has recorded a timeout. Waits for work
+// that completes by itself (copies in flight, issued MMAs) are not abortable, so that the CTA
+// never frees tensor memory or exits under them.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status,
+                                          bool abortable = true) {
+  if (mbar_test(b, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_test(b, parity)) return true;
+    if ((i & 255u) == 0 && (now_ns() - t0 > kWaitNs || (abortable && aborted(status)))) {
+      atomicOr(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(1) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
+         (static_cast<uint64_t>(2) << 61);
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 consecutive FP32 columns of tensor memory into 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Split one FP32 A tile (staging, TMA layout) into P bf16 tiles in the K-major 128-byte
+// swizzled layout: row m at byte m*128, 16-byte chunk c (columns 8c..8c+7) at chunk c ^ (m%8).
+template <int P, bool TRANS>
+__device__ __forceinline__ void split_tile(const float* st, uint8_t* slices, int ct) {
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int idx = ct + 128 * it;
+    int m, c;
+    float v[8];
+    if (!TRANS) {             // staging [m][k]: 8 lanes read one 256-byte row
+      c = idx & 7;
+      m = idx >> 3;
+      const float4 lo = *reinterpret_cast<const float4*>(st + m * BK + 8 * c);
+      const float4 hi = *reinterpret_cast<const float4*>(st + m * BK + 8 * c + 4);
+      v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+      v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+    } else {                  // staging [k][m]: a warp reads 32 consecutive m
+      m = idx & (BM - 1);
+      c = idx >> 7;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = st[(8 * c + e) * BM + m];
+    }
+    uint32_t w[P][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float x0 = v[2 * e], x1 = v[2 * e + 1];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        w[p][e] = *reinterpret_cast<const uint32_t*>(&h);
+        const float2 f = __bfloat1622float2(h);
+        x0 -= f.x;
+        x1 -= f.y;
+      }
+    }
+    const uint32_t off = static_cast<uint32_t>(m) * 128u +
+                         ((static_cast<uint32_t>(c) ^ (static_cast<uint32_t>(m) & 7u)) << 4);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      *reinterpret_cast<uint4*>(slices + p * kSliceABytes + off) =
+          make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+}
+
+struct TcArgs {
+  int M, K;        // rows of C, reduction length
+  int BN;          // columns per CTA (multiple of 32, <= 128); blockIdx.z picks the column tile
+  int BNt;         // padded columns of the whole product (BN x column tiles)
+  int kchunk;      // reduction columns per split (multiple of BK)
+  double* partial; // [splits][M][BNt] FP64
+  int* status;
+};
+
+template <int P, int Q, bool TRANS, int SA, int SO, int DR>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    sliced_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  if (aborted(a.status)) return;              // a CTA of this or an earlier launch timed out
+  uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
+  const int BN = a.BN;
+  const int slice_b_bytes = BN * 128;
+  uint8_t* stA = smem;                                           // SA FP32 staging tiles
+  uint8_t* opA = stA + SA * kStageABytes;                        // SO x P bf16 A slices
+  uint8_t* opB = opA + SO * P * kSliceABytes;                    // SO x Q bf16 B slices
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(opB + SO * Q * slice_b_bytes);
+  uint64_t* a_empty = a_full + SA;
+  uint64_t* b_full = a_empty + SA;
+  uint64_t* o_empty = b_full + SO;
+  uint64_t* a_ready = o_empty + SO;
+  uint64_t* acc_full = a_ready + SO;                             // 2: accumulator ping-pong
+  uint64_t* acc_empty = acc_full + 2;                            // 2
+  uint64_t* mma_done = acc_empty + 2;                            // every issued MMA finished
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int m0 = blockIdx.x * BM;
+  const int n0 = blockIdx.z * BN;                                // first column of this tile
+  const int k_begin = blockIdx.y * a.kchunk;
+  const int k_end = min(a.K, k_begin + a.kchunk);
+  const int nk = (k_end - k_begin + BK - 1) / BK;
+  const int ngroups = (nk + DR - 1) / DR;                        // accumulator drains
+  constexpr uint32_t kTmemCols = 512;                            // acc0, acc1, hi, lo
+  constexpr uint32_t kHi = 256, kLo = 384;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < SA; ++i) {
+      mbar_init(&a_full[i], 1);
+      mbar_init(&a_empty[i], 4);
+    }
+    for (int i = 0; i < SO; ++i) {
+      mbar_init(&b_full[i], 1);
+      mbar_init(&o_empty[i], 1);
+      mbar_init(&a_ready[i], 4);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {                                            // ---- TMA producer ----
+      bool ok = true;
+      int issued_a = 0, issued_b = 0;
+      for (int ks = 0; ks < nk && ok; ++ks) {
+        const int sa = ks % SA, ua = ks / SA, so = ks % SO, uo = ks / SO;
+        const int k0 = k_begin + ks * BK;
+        if (ks >= SA) ok = mbar_wait(&a_empty[sa], (ua - 1) & 1, a.status);
+        if (!ok) break;
+        mbar_expect_tx(&a_full[sa], kStageABytes);
+        if (!TRANS) tma_load_2d(stA + sa * kStageABytes, &tmA, &a_full[sa], k0, m0);
+        else tma_load_2d(stA + sa * kStageABytes, &tmA, &a_full[sa], m0, k0);
+        issued_a = ks + 1;
+        if (ks >= SO) ok = mbar_wait(&o_empty[so], (uo - 1) & 1, a.status);
+        if (!ok) break;
+        mbar_expect_tx(&b_full[so], Q * slice_b_bytes);
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+          tma_load_2d(opB + (so * Q + q) * slice_b_bytes, &tmB, &b_full[so], k0, q * a.BNt + n0);
+        issued_b = ks + 1;
+      }
+      // the last copies into each buffer must have landed before the CTA may exit
+      for (int ks = max(0, issued_a - SA); ks < issued_a; ++ks)
+        mbar_wait(&a_full[ks % SA], (ks / SA) & 1, a.status, false);
+      for (int ks = max(0, issued_b - SO); ks < issued_b; ++ks)
+        mbar_wait(&b_full[ks % SO], (ks / SO) & 1, a.status, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {                                            // ---- MMA issuer ----
+      const uint32_t idesc = idesc_bf16(BM, BN);
+      bool ok = true;
+      int committed = 0;                                        // accumulator groups committed
+      for (int g = 0; g < ngroups && ok; ++g) {
+        const int b = g & 1;
+        if (g >= 2) ok = mbar_wait(&acc_empty[b], ((g >> 1) - 1) & 1, a.status);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + static_cast<uint32_t>(b * 128);
+        const int ks_end = min(nk, (g + 1) * DR);
+        for (int ks = g * DR; ks < ks_end && ok; ++ks) {
+          const int so = ks % SO, uo = ks / SO;
+          ok = mbar_wait(&b_full[so], uo & 1, a.status) && mbar_wait(&a_ready[so], uo & 1, a.status);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t abase = su32(opA + so * P * kSliceABytes);
+          const uint32_t bbase = su32(opB + so * Q * slice_b_bytes);
+          const bool fresh = (ks == g * DR);
+          int term = 0;
+          // small slice products first, the leading pair (0, 0) last
+#pragma unroll
+          for (int level = (P > Q ? P : Q) - 1; level >= 0; --level) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+              const int q = level - p;
+              if (q < 0 || q >= Q) continue;
+              const uint64_t ad = sw128_desc(abase + p * kSliceABytes);
+              const uint64_t bd = sw128_desc(bbase + q * slice_b_bytes);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (fresh && term == 0 && kk == 0) ? 0u : 1u);
+              ++term;
+            }
+          }
+          mma_commit(&o_empty[so]);
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[b]);
+        committed = g + 1;
+      }
+      (void)committed;
+      // every MMA this thread issued must have finished before tensor memory is freed
+      mma_commit(mma_done);
+      mbar_wait(mma_done, 0, a.status, false);
+    }
+  } else if (warp < 6) {                                        // ---- A splitters ----
+    const int ct = threadIdx.x - 64;
+    bool ok = true;
+    for (int ks = 0; ks < nk && ok; ++ks) {
+      const int sa = ks % SA, ua = ks / SA, so = ks % SO, uo = ks / SO;
+      ok = mbar_wait(&a_full[sa], ua & 1, a.status);
+      if (ok && ks >= SO) ok = mbar_wait(&o_empty[so], (uo - 1) & 1, a.status);
+      if (!ok) break;
+      split_tile<P, TRANS>(reinterpret_cast<const float*>(stA + sa * kStageABytes),
+                           opA + so * P * kSliceABytes, ct);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&a_empty[sa]);
+        mbar_arrive(&a_ready[so]);
+      }
+    }
+  } else {                                                      // ---- accumulator drain ----
+    const int quarter = warp & 3;                               // TMEM lanes 32*quarter..+31
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    bool ok = true;
+    int drained = 0;
+    for (int g = 0; g < ngroups && ok; ++g) {
+      const int b = g & 1;
+      ok = mbar_wait(&acc_full[b], (g >> 1) & 1, a.status);
+      if (!ok) break;
+      tc_fence_after();
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t x[32], hi[32], lo[32];
+        tmem_ld32(tmem + lane_base + static_cast<uint32_t>(b * 128 + c0), x);
+        if (g == 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            hi[j] = x[j];
+            lo[j] = 0u;
+          }
+        } else {
+          tmem_ld32(tmem + lane_base + kHi + static_cast<uint32_t>(c0), hi);
+          tmem_ld32(tmem + lane_base + kLo + static_cast<uint32_t>(c0), lo);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {                        // (hi, lo) += x, TwoSum
+            const float h = __uint_as_float(hi[j]), v = __uint_as_float(x[j]);
+            const float s = h + v;
+            const float bp = s - h;
+            const float err = (h - (s - bp)) + (v - bp);
+            hi[j] = __float_as_uint(s);
+            lo[j] = __float_as_uint(__uint_as_float(lo[j]) + err);
+          }
+        }
+        tmem_st32(tmem + lane_base + kHi + static_cast<uint32_t>(c0), hi);
+        tmem_st32(tmem + lane_base + kLo + static_cast<uint32_t>(c0), lo);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      drained = g + 1;
+    }
+    tc_fence_after();
+    const int row = m0 + quarter * 32 + lane;
+    double* out = a.partial + (static_cast<size_t>(blockIdx.y) * a.M + row) * a.BNt + n0;
+    if (ok && drained == ngroups && ngroups > 0) {
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t hi[32], lo[32];
+        tmem_ld32(tmem + lane_base + kHi + static_cast<uint32_t>(c0), hi);
+        tmem_ld32(tmem + lane_base + kLo + static_cast<uint32_t>(c0), lo);
+        if (row < a.M) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 2)
+            *reinterpret_cast<double2*>(out + c0 + j) = make_double2(
+                static_cast<double>(__uint_as_float(hi[j])) + static_cast<double>(__uint_as_float(lo[j])),
+                static_cast<double>(__uint_as_float(hi[j + 1])) + static_cast<double>(__uint_as_float(lo[j + 1])));
+        }
+      }
+    } else if (ngroups == 0 && row < a.M) {
+      for (int c = 0; c < BN; ++c) out[c] = 0.0;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// Omega (N x s FP64, row-major) -> Q bf16 slices of Omega^*: out[q*BN + c][j], rows c >= s and
+// columns j >= N zero. 32 x 32 tiles through shared memory so both sides stay coalesced.
+template <int Q>
+__global__ void split_rhs(const double* __restrict__ X, int64_t N, int s, int BN, int64_t ldb,
+                          __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int64_t j0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int c0 = blockIdx.y * 32;
+  for (int e = threadIdx.y; e < 32; e += blockDim.y) {
+    const int64_t j = j0 + e;
+    const int c = c0 + threadIdx.x;
+    tile[e][threadIdx.x] = (j < N && c < s) ? X[j * s + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.y; e < 32; e += blockDim.y) {
+    const int c = c0 + e;
+    const int64_t j = j0 + threadIdx.x;
+    if (c >= BN || j >= ldb) continue;
+    double x = tile[threadIdx.x][e];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const __nv_bfloat16 h = __double2bfloat16(x);
+      out[(static_cast<int64_t>(q) * BN + c) * ldb + j] = h;
+      x -= static_cast<double>(__bfloat162float(h));
+    }
+  }
+}
+
+__global__ void reduce_partials(const double* __restrict__ partial, int splits, int64_t M, int BN,
+                                int s, double* __restrict__ C) {
+  const int64_t total = M * s;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / s;
+    const int c = static_cast<int>(idx % s);
+    double acc = 0.0;
+    for (int sp = 0; sp < splits; ++sp) acc += partial[(sp * M + i) * BN + c];
+    C[idx] = acc;
+  }
+}
+
+// ---- host side ------------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+              uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+              CUtensorMapSwizzle swz) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Per-device scratch of the tensor-core sampling (B slices and split partials), grown on demand.
+struct TcScratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_tc_mutex;
+std::vector<TcScratch> g_tc_scratch;
+
+cudaError_t tc_scratch(size_t bytes, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_tc_mutex);
+  if (static_cast<int>(g_tc_scratch.size()) <= dev) g_tc_scratch.resize(dev + 1);
+  TcScratch& s = g_tc_scratch[dev];
+  if (s.bytes < bytes) {
+    if (s.ptr) {
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return e;
+      cudaFree(s.ptr);
+      s.ptr = nullptr;
+      s.bytes = 0;
+    }
+    e = cudaMalloc(&s.ptr, bytes);
+    if (e != cudaSuccess) return e;
+    s.bytes = bytes;
+    e = cudaMemset(s.ptr, 0, 1024);          // status word starts clear
+    if (e != cudaSuccess) return e;
+  }
+  *out = s.ptr;
+  return cudaSuccess;
+}
+
+size_t smem_bytes(int P, int Q, int SA, int SO, int BN) {
+  return static_cast<size_t>(SA) * kStageABytes + static_cast<size_t>(SO) * P * kSliceABytes +
+         static_cast<size_t>(SO) * Q * BN * 128 + 256 + 1024;
+}
+
+template <int P, int Q, bool TRANS, int SA, int SO>
+cudaError_t launch_one(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args,
+                       int splits, cudaStream_t st) {
+  constexpr int DR = (P >= 3) ? 1 : 2;        // reduction steps per accumulator drain
+  auto kernel = sliced_gemm_tc<P, Q, TRANS, SA, SO, DR>;
+  const size_t bytes = smem_bytes(P, Q, SA, SO, args.BN);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(static_cast<unsigned>((args.M + BM - 1) / BM), static_cast<unsigned>(splits),
+                  static_cast<unsigned>(args.BNt / args.BN));
+  kernel<<<grid, kTcThreads, bytes, st>>>(ma, mb, args);
+  return cudaGetLastError();
+}
+
+template <int P, bool TRANS>
+cudaError_t launch_pq(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args, int splits,
+                      cudaStream_t st) {
+  // stage counts that fit 227 KB: FP32 staging double-buffered, operand stages 2 when they fit
+  if (smem_bytes(P, P, 2, 2, args.BN) <= kMaxNodeSmemBytes)
+    return launch_one<P, P, TRANS, 2, 2>(ma, mb, args, splits, st);
+  return launch_one<P, P, TRANS, 2, 1>(ma, mb, args, splits, st);
+}
+
+}  // namespace
+
+// Column tiling: s <= 128 runs as one tile of BN = s rounded up to 32; wider s as tiles of 128.
+void column_tiles(int s, int* BN, int* BNt) {
+  *BNt = (s <= 128) ? (s + 31) / 32 * 32 : (s + 127) / 128 * 128;
+  *BN = (*BNt < 128) ? *BNt : 128;
+}
+
+// Reduction splits: only to fill the GPU (about 8 CTAs per SM in total), each split >= 64 wide.
+int reduction_splits(int64_t N, int BNt, int BN) {
+  const int64_t tiles = ((N + BM - 1) / BM) * (BNt / BN);
+  int64_t splits = (8 * 152 + tiles - 1) / tiles;
+  const int64_t ksteps = (N + BK - 1) / BK;
+  if (splits > ksteps) splits = ksteps;
+  return static_cast<int>(splits < 1 ? 1 : splits);
+}
+
+// Scratch layout: [0, 1024) status word; then Q x BNt x ldb bf16 slices of Omega^* and of
+// Psi^*; then the FP64 split partials.
+size_t sample_tc_scratch_bytes(int64_t N, int s, int kchunk) {
+  int BN, BNt;
+  column_tiles(s, &BN, &BNt);
+  const int64_t ldb = (N + 7) / 8 * 8;
+  const int64_t splits = (N + kchunk - 1) / kchunk;
+  return 1024 + static_cast<size_t>(2 * 3 * BNt * ldb * 2) +
+         static_cast<size_t>(splits * N * BNt * 8);
+}
+
+cudaError_t sample_tc_status(int* host_status, bool clear) {
+  *host_status = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int* status = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_tc_mutex);
+    if (dev < static_cast<int>(g_tc_scratch.size())) status = static_cast<int*>(g_tc_scratch[dev].ptr);
+  }
+  if (!status) return cudaSuccess;
+  e = cudaMemcpy(host_status, status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(status, 0, sizeof(int));
+  return e;
+}
+
+cudaError_t launch_sample_dense_tc(const float* A, int64_t lda, int64_t N, const double* Om,
+                                   const double* Ps, int s, double* Y, double* Z, int slices,
+                                   int kchunk_hint, cudaStream_t st) {
+  if (slices != 2 && slices != 3) return cudaErrorInvalidValue;
+  if (s < 1 || s > 256 || N < 1 || N > (int64_t(1) << 30) || lda % 4 != 0)
+    return cudaErrorInvalidValue;
+  int BN, BNt;
+  column_tiles(s, &BN, &BNt);
+  const int64_t ldb = (N + 7) / 8 * 8;
+  int kchunk;
+  if (kchunk_hint > 0) {
+    kchunk = (kchunk_hint + BK - 1) / BK * BK;
+  } else {
+    const int splits_wanted = reduction_splits(N, BNt, BN);
+    kchunk = static_cast<int>(((N + splits_wanted - 1) / splits_wanted + BK - 1) / BK * BK);
+  }
+  const int splits = static_cast<int>((N + kchunk - 1) / kchunk);
+  void* scratch = nullptr;
+  cudaError_t e = tc_scratch(sample_tc_scratch_bytes(N, s, kchunk), &scratch);
+  if (e != cudaSuccess) return e;
+  int* status = static_cast<int*>(scratch);
+  auto* bY = reinterpret_cast<__nv_bfloat16*>(static_cast<uint8_t*>(scratch) + 1024);
+  auto* bZ = bY + 3 * BNt * ldb;
+  double* partial = reinterpret_cast<double*>(bZ + 3 * BNt * ldb);
+
+  const dim3 tb(32, 8), tg(static_cast<unsigned>((ldb + 31) / 32), static_cast<unsigned>((BNt + 31) / 32));
+  if (slices == 2) {
+    split_rhs<2><<<tg, tb, 0, st>>>(Om, N, s, BNt, ldb, bY);
+    split_rhs<2><<<tg, tb, 0, st>>>(Ps, N, s, BNt, ldb, bZ);
+  } else {
+    split_rhs<3><<<tg, tb, 0, st>>>(Om, N, s, BNt, ldb, bY);
+    split_rhs<3><<<tg, tb, 0, st>>>(Ps, N, s, BNt, ldb, bZ);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  CUtensorMap mAy, mAz, mBy, mBz;
+  const uint64_t arow = static_cast<uint64_t>(lda) * 4;
+  const uint64_t brow = static_cast<uint64_t>(ldb) * 2;
+  const uint64_t brows = static_cast<uint64_t>(slices) * BNt;
+  if (!make_map(&mAy, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, N, N, arow, BK, BM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+      !make_map(&mAz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, N, N, arow, BM, BK, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+      !make_map(&mBy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bY, N, brows, brow, BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map(&mBz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bZ, N, brows, brow, BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+
+  TcArgs args{static_cast<int>(N), static_cast<int>(N), BN, BNt, kchunk, partial, status};
+  const unsigned rg = 152u * 8u;
+  e = (slices == 2) ? launch_pq<2, false>(mAy, mBy, args, splits, st)
+                    : launch_pq<3, false>(mAy, mBy, args, splits, st);
+  if (e != cudaSuccess) return e;
+  reduce_partials<<<rg, 256, 0, st>>>(partial, splits, N, BNt, s, Y);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = (slices == 2) ? launch_pq<2, true>(mAz, mBz, args, splits, st)
+                    : launch_pq<3, true>(mAz, mBz, args, splits, st);
+  if (e != cudaSuccess) return e;
+  reduce_partials<<<rg, 256, 0, st>>>(partial, splits, N, BNt, s, Z);
+  return cudaGetLastError();
+}
+
+}  // namespace hbs

@@ -14,7 +14,8 @@
 // Omega_tau = L_1 Q_1^* with L_1 the leading n x n lower triangle, Omega^+ = Q_1 L_1^{-1}.
 // Each row y of Y_tau is pushed once through all n reflectors (y Q = y H_0 ... H_{n-1}):
 // its last r entries are the row of Y_tau P, and its first n entries, solved against L_1,
-// are the row of Y_tau Omega^+. Neither P nor Q is formed. col(., r) is an unpivoted
+// are the row of Y_tau Omega^+. The factored block keeps L_1's strictly lower part in place,
+// its diagonal as reciprocals in `rdiag`, and each reflector with an explicit leading 1. Neither P nor Q is formed. col(., r) is an unpivoted
 // Householder QR whose first r orthonormal columns are formed explicitly. Reflectors use
 // LAPACK's sign choice (beta = -sign(alpha) ||x||; identity when the tail is zero).
 //
@@ -52,9 +53,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Reflector of row j of M over columns j..cols-1 (warp 0 only). Leaves beta_j in M[j][j] and
-// the tail of v_j (v_j[j] = 1 implied) in M[j][j+1..], tau_j in tau[j]; with rdiag, also
-// 1/beta_j and a NUMERIC flag if beta_j is zero or not finite.
+// Reflector of row j of M over columns j..cols-1 (warp 0 only). Leaves v_j in M[j][j..] with
+// the leading 1 stored explicitly (so that applying it needs no special case), tau_j in tau[j];
+// with rdiag, also 1/beta_j (the diagonal of L) and a NUMERIC flag if beta_j is zero or not
+// finite.
 __device__ void make_reflector(double* M, int ld, int j, int cols, double* tau, double* rdiag,
                                int* status) {
   if (threadIdx.x >= 32) return;
@@ -71,8 +73,9 @@ __device__ void make_reflector(double* M, int ld, int j, int cols, double* tau, 
     scale = 1.0 / (alpha - beta);
   }
   for (int k = j + 1 + lane; k < cols; k += 32) row[k] *= scale;
+  __syncwarp();
   if (lane == 0) {
-    row[j] = beta;
+    row[j] = 1.0;
     tau[j] = t;
     if (rdiag != nullptr) {
       rdiag[j] = 1.0 / beta;
@@ -95,19 +98,19 @@ __device__ void lq_factor(double* M, int ld, int rows, int cols, double* tau, do
       const int i = j + 1 + base + gid;
       const bool active = i < rows;
       double* ri = M + static_cast<size_t>(active ? i : j) * ld;
-      double part = (q == 0) ? ri[j] : 0.0;
-      for (int k = j + 1 + q; k < cols; k += G) part = fma(ri[k], v[k], part);
+      double part = 0.0;
+      for (int k = j + q; k < cols; k += G) part = fma(ri[k], v[k], part);
       const double w = group_sum(part) * tj;
-      if (active) {
-        if (q == 0) ri[j] -= w;
-        for (int k = j + 1 + q; k < cols; k += G) ri[k] = fma(-w, v[k], ri[k]);
-      }
+      if (active)
+        for (int k = j + q; k < cols; k += G) ri[k] = fma(-w, v[k], ri[k]);
     }
     __syncthreads();
   }
 }
 
-// y <- y H_j for the reflector stored in row j of M (columns j..cols-1).
+// y <- y H_j for the reflector stored in row j of M (columns j..cols-1, leading 1 explicit).
+// Slots wholly left of column j are skipped (warp-uniform); inside the boundary slot the
+// columns k < j select a zero, so every slot costs exactly one FP64 instruction per pass.
 template <int T>
 __device__ __forceinline__ void apply_reflector(double (&y)[T], const double* v, double tj, int j,
                                                 int cols, int q) {
@@ -116,16 +119,16 @@ __device__ __forceinline__ void apply_reflector(double (&y)[T], const double* v,
   for (int t = 0; t < T; ++t) {
     if (G * t + G - 1 < j || G * t >= cols) continue;
     const int k = q + G * t;
-    if (k > j && k < cols) part = fma(y[t], v[k], part);
-    else if (k == j) part += y[t];
+    const double vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : 0.0;
+    part = fma(y[t], vk, part);
   }
   const double w = group_sum(part) * tj;
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     if (G * t + G - 1 < j || G * t >= cols) continue;
     const int k = q + G * t;
-    if (k > j && k < cols) y[t] = fma(-w, v[k], y[t]);
-    else if (k == j) y[t] -= w;
+    const double vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : 0.0;
+    y[t] = fma(-w, vk, y[t]);
   }
 }
 

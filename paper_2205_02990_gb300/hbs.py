@@ -25,13 +25,15 @@ HBS_ERR_TIMEOUT = -6
 HBS_ERR_CALLBACK = -7
 HBS_ERR_UNSUPPORTED = -8
 HBS_PREC_FP64 = 0
+HBS_PREC_MIXED_BF16X3 = 1
+HBS_PREC_MIXED_BF16X6 = 2
 HBS_F64 = 0
 HBS_F32 = 1
 
 EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan", "hbs_execute", "hbs_compress",
             "hbs_apply", "hbs_sync_status", "hbs_free", "hbs_last_error", "hbs_tree",
             "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
-            "hbs_apply_static"]
+            "hbs_apply_static", "hbs_sample_sync"]
 
 
 class HBSError(RuntimeError):
@@ -74,6 +76,7 @@ def load():
                                  c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
         "hbs_sample_products": (c.c_int, [c.POINTER(_Operator), c.c_int32, c.c_int32, c.c_void_p,
                                           c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "hbs_sample_sync": (c.c_int, [c.c_void_p]),
         "hbs_plan": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p)]),
         "hbs_execute": (c.c_int, [c.c_void_p, c.POINTER(_Problem), c.c_void_p]),
         "hbs_compress": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p),
@@ -128,11 +131,12 @@ def hbs_draw_gaussian(N, s, stream_id, seed, out):
 def _operator(A, N):
     """(ctypes operator, keep-alive) for a dense CUDA float64 tensor or a callable black box."""
     if isinstance(A, torch.Tensor):
-        if (not A.is_cuda or A.dtype != torch.float64 or A.dim() != 2 or A.shape[0] != A.shape[1]
-                or A.stride(1) != 1 or A.stride(0) < A.shape[0]):
-            raise TypeError("A must be a square row-major CUDA float64 matrix")
+        if (not A.is_cuda or A.dtype not in (torch.float64, torch.float32) or A.dim() != 2
+                or A.shape[0] != A.shape[1] or A.stride(1) != 1 or A.stride(0) < A.shape[0]):
+            raise TypeError("A must be a square row-major CUDA float64 or float32 matrix")
         N = A.shape[0]
-        op = _Operator(N=N, dtype=HBS_F64, A=A.data_ptr(), lda=A.stride(0), fn=MATMAT_FN(), user=None)
+        dt = HBS_F64 if A.dtype == torch.float64 else HBS_F32
+        op = _Operator(N=N, dtype=dt, A=A.data_ptr(), lda=A.stride(0), fn=MATMAT_FN(), user=None)
         return op, None, N
     if N is None:
         raise ValueError("N is required with a callable operator")
@@ -159,6 +163,11 @@ def hbs_sample(A, s, seed, Omega, Psi, Y, Z, precision=HBS_PREC_FP64, N=None):
     ptrs = [_dev(x, (N, s), nm) for x, nm in ((Omega, "Omega"), (Psi, "Psi"), (Y, "Y"), (Z, "Z"))]
     _check(load().hbs_sample(ctypes.byref(op), s, seed, precision, *ptrs, _stream()))
     del keep
+
+
+def hbs_sample_sync():
+    """Wait for the current stream; raise if the tensor-core sampling reported a timeout."""
+    _check(load().hbs_sample_sync(_stream()))
 
 
 def hbs_sample_products(A, s, Omega, Psi, Y, Z, precision=HBS_PREC_FP64, N=None):
