@@ -134,8 +134,12 @@ typedef struct hbs_handle hbs_handle;   /* opaque: owns the factors and all work
 /* Plan a batch of compressions: validates every problem, builds every tree and allocates the
  * device arena for the factors and workspace. Queues no work. Admissible shapes (Section 4
  * asks for s >= max(r + m, 3r)): with L >= 1, every leaf has between r and s - r rows and
- * s >= 3r; with L = 0 (N <= leaf_max), N <= s. This build also needs the per-node shared-memory
- * tile to fit: n (s + 1) + r n <= 28672 doubles for every node of n rows (s <= ~160 at r = 50).
+ * s >= 3r; with L = 0 (N <= leaf_max), N <= s. This build also needs s <= 192 and the per-node
+ * shared-memory tiles to fit: n (s + 1) + 2n <= 29056 and (r + n)(n + 1) + r n + r <= 29056
+ * doubles for every node of n rows.
+ * Sweep precision: HBS_PREC_FP64 keeps every step in FP64; the mixed precisions keep the LQ of
+ * each test block (nullspace and pseudo-inverse) and the sample rows pushed through it in FP64
+ * and compute the bases, D_tau and the parent blocks in FP32 (factors stored in FP64).
  * Errors: HBS_ERR_ARG, HBS_ERR_SHAPE, HBS_ERR_UNSUPPORTED, HBS_ERR_NOMEM, HBS_ERR_CUDA.
  */
 int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out);

@@ -73,7 +73,7 @@ struct Item {
   int64_t N = 0;
   int r = 0, s = 0, leaf_max = 0, L = 0;
   std::vector<int64_t> off, size;
-  std::vector<int64_t> oU, oV, oD, oWY, oWZ, oOm, oPs, oY, oZ;   // arena offsets by node id
+  std::vector<int64_t> oU, oV, oD, oWY, oWZ, oXY, oXZ, oOm, oPs, oY, oZ;   // arena offsets
   const double *Om = nullptr, *Ps = nullptr, *Y = nullptr, *Z = nullptr;
   int64_t node_rows(int64_t t) const { return level_of(t) == L ? size[t] : 2 * r; }
   int level_of(int64_t t) const {
@@ -132,7 +132,8 @@ int check_problem(const hbs_problem& p, int idx) {
   if (p.s > hbs::kMaxS)
     return fail(HBS_ERR_UNSUPPORTED, "problem %d: s = %d exceeds %d", idx, p.s, hbs::kMaxS);
   const int64_t nmax = (L == 0) ? p.N : std::max<int64_t>(2 * p.r, size[int64_t(1) << L]);
-  if (hbs::node_smem_doubles(int(nmax), p.r, p.s) * sizeof(double) > hbs::kMaxNodeSmemBytes)
+  if (hbs::side_smem_doubles(int(nmax), p.s) * sizeof(double) > hbs::kMaxNodeSmemBytes ||
+      hbs::finish_smem_reals(int(nmax), p.r) * sizeof(double) > hbs::kMaxNodeSmemBytes)
     return fail(HBS_ERR_UNSUPPORTED, "problem %d: node tile of %lld x %d exceeds shared memory",
                 idx, (long long)nmax, p.s);
   return HBS_OK;
@@ -172,6 +173,8 @@ void build_tasks(hbs_handle* h) {
           tk.V = h->arena + it.oV[t];
           tk.WY = h->arena + it.oWY[t];
           tk.WZ = h->arena + it.oWZ[t];
+          tk.XY = h->arena + it.oXY[t];
+          tk.XZ = h->arena + it.oXZ[t];
           const int64_t p = t / 2, row = (t % 2) * int64_t(r) * s;
           tk.Om_p = h->arena + it.oOm[p] + row;
           tk.Ps_p = h->arena + it.oPs[p] + row;
@@ -303,8 +306,9 @@ int hbs_sample(const hbs_operator* op, int32_t s, uint64_t seed, int32_t precisi
 int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out) {
   if (!out || !probs || batch < 1) return fail(HBS_ERR_ARG, "hbs_plan: bad arguments");
   *out = nullptr;
-  if (precision != HBS_PREC_FP64)
-    return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: sweep precision %d not built", precision);
+  if (precision != HBS_PREC_FP64 && precision != HBS_PREC_MIXED_BF16X3 &&
+      precision != HBS_PREC_MIXED_BF16X6)
+    return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: unknown precision %d", precision);
   for (int i = 0; i < batch; ++i) {
     const int rc = check_problem(probs[i], i);
     if (rc != HBS_OK) return rc;
@@ -323,7 +327,8 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
     it.leaf_max = p.leaf_max;
     build_tree(p.N, p.leaf_max, &it.L, &it.off, &it.size);
     const int64_t count = int64_t(2) << it.L;
-    for (auto* v : {&it.oU, &it.oV, &it.oD, &it.oWY, &it.oWZ, &it.oOm, &it.oPs, &it.oY, &it.oZ})
+    for (auto* v : {&it.oU, &it.oV, &it.oD, &it.oWY, &it.oWZ, &it.oXY, &it.oXZ, &it.oOm, &it.oPs,
+                    &it.oY, &it.oZ})
       v->assign(count, -1);
     for (int64_t t = 1; t < count; ++t) {
       const int64_t n = (it.L == 0) ? it.N : it.node_rows(t);
@@ -347,6 +352,10 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
       cursor += size_t(n) * n;
       it.oWZ[t] = int64_t(cursor);
       cursor += size_t(n) * n;
+      it.oXY[t] = int64_t(cursor);
+      cursor += size_t(n) * it.r;
+      it.oXZ[t] = int64_t(cursor);
+      cursor += size_t(n) * it.r;
     }
     for (int64_t t = 1; t < (int64_t(1) << it.L); ++t) {
       const size_t blk = size_t(2) * it.r * it.s;
@@ -395,10 +404,11 @@ int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream) {
     if (rc != HBS_OK) return rc;
     h->tasks_uploaded = true;
   }
+  const bool fp32_finish = h->precision != HBS_PREC_FP64;
   for (auto& H : h->heights) {
-    cudaError_t e = hbs::launch_node_sweep_f64(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
-                                               H.max_s, h->d_status, st);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep kernel");
+    cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
+                                            H.max_s, fp32_finish, h->d_status, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep kernels");
   }
   return ok();
 }

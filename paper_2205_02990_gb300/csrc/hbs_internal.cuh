@@ -22,6 +22,8 @@ struct NodeTask {
   double* D;          // n x n output block D_tau
   double* WY;         // n x n workspace: Y_tau Omega_tau^dagger
   double* WZ;         // n x n workspace: Z_tau Psi_tau^dagger
+  double* XY;         // n x r workspace: Y_tau P_tau
+  double* XZ;         // n x r workspace: Z_tau Q_tau
   double* Om_p;       // this node's r x s rows of the parent's blocks (leading dimension s):
   double* Ps_p;       //   left child rows 0..r-1, right child rows r..2r-1; unused at the root
   double* Y_p;
@@ -42,13 +44,16 @@ struct GemmTask {
   int32_t t1, t2;                       // 1 = transpose
 };
 
-// Shared-memory doubles for one node of n rows (sweep kernel).
-size_t node_smem_doubles(int n, int r, int s);
+// Shared memory of the sweep kernels for a node of n rows (sweep.cu).
+size_t side_smem_doubles(int n, int s);
+size_t finish_smem_reals(int n, int r);
 constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
 
-cudaError_t launch_node_sweep_f64(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
-                                  int max_s, int* d_status, cudaStream_t st);
+// One tree height of Algorithm 2: the side kernel (FP64) then the finish kernel (FP64, or FP32
+// when fp32_finish).
+cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
+                               int max_s, bool fp32_finish, int* d_status, cudaStream_t st);
 cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, double* out,
                             cudaStream_t st);
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,

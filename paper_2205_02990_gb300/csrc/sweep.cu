@@ -1,0 +1,411 @@
+// Per-level sweep of Algorithm 2: two kernels per tree level.
+//
+// For a node tau with blocks Omega_tau, Psi_tau, Y_tau, Z_tau (n x s) the sweep computes
+//   P = null(Omega_tau, r), U = col(Y_tau P, r)              (Section 4.1, Eq. u_tau_formula)
+//   Q = null(Psi_tau, r),   V = col(Z_tau Q, r)              (Eq. v_tau_formula)
+//   D = (I - UU^*) Y Omega^+ + UU^* ((I - VV^*) Z Psi^+)^*   (Eq. d_tau_formula)
+// and the node's rows of the parent's blocks (Eq. omega_tau_and_y_tau, Algorithm 2):
+//   V^* Omega_tau, U^* Psi_tau, U^* (Y_tau - D Omega_tau), V^* (Z_tau - D^* Psi_tau).
+// At the root only D = Y Omega^+ (Section 4.3).
+//
+// Side kernel (FP64 in every precision: it holds the nullspace and the pseudo-inverse). One
+// CTA per (node, side, slice of rows); side 0 works on Omega_tau and Y_tau, side 1 on Psi_tau
+// and Z_tau. One Householder LQ of the test block, Omega_tau = L Q^* (the QR of Omega_tau^* of
+// Section 2.4, Q square), serves both `null` and the pseudo-inverse: the last r columns of Q
+// are null(Omega_tau, r), and Omega_tau = L_1 Q_1^* with L_1 the leading n x n lower triangle
+// gives Omega^+ = Q_1 L_1^{-1}. Each sample row y is pushed once through the n reflectors
+// (y Q = y H_0 ... H_{n-1}): its last r entries are the row of Y_tau P, its first n entries,
+// solved against L_1, the row of Y_tau Omega^+. Neither P nor Q is formed. Where a level has
+// few nodes, the rows are split across several CTAs (each refactors the small test block), so
+// that the upper levels of the tree still fill the GPU.
+//
+// Finish kernel (FP64, or FP32 in the mixed precisions): one CTA per node. col(., r) is an
+// unpivoted Householder QR whose first r columns are formed explicitly, then D_tau and the
+// parent's blocks. Since UU^* U = U, the product U^* D needed by the merge equals U^* T2^*
+// with T2 = (I - VV^*) Z Psi^+ and is taken from there; D V is formed from D.
+//
+// Reflectors use LAPACK's sign choice (beta = -sign(alpha) ||x||; identity when the tail is
+// zero) and are stored with their leading 1 explicit. Mapping: 256 threads = 32 groups of 8
+// lanes; a group owns one row (of the factored block, of a streamed sample row, or of a basis
+// column) and lane q of a group holds columns q, q + 8, ... Reductions inside a group take 3
+// shuffles. The FP64 pipe (2 DFMA per clock per SM on GB300) bounds the side kernel.
+#include <algorithm>
+
+#include "hbs_internal.cuh"
+
+namespace hbs {
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int G = 8;                    // lanes per row
+constexpr int NGROUPS = THREADS / G;    // rows processed at once
+constexpr unsigned FULL = 0xffffffffu;
+
+template <class Real>
+__device__ __forceinline__ Real group_sum(Real v) {
+  v += __shfl_xor_sync(FULL, v, 4);
+  v += __shfl_xor_sync(FULL, v, 2);
+  v += __shfl_xor_sync(FULL, v, 1);
+  return v;
+}
+
+template <class Real>
+__device__ __forceinline__ Real warp_sum(Real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Reflector of row j of M over columns j..cols-1 (warp 0 only). Leaves v_j in M[j][j..] with
+// the leading 1 stored explicitly, tau_j in tau[j]; with rdiag, also 1/beta_j (the diagonal of
+// L) and a NUMERIC flag if beta_j is zero or not finite.
+template <class Real>
+__device__ void make_reflector(Real* M, int ld, int j, int cols, Real* tau, Real* rdiag,
+                               int* status) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  Real* row = M + static_cast<size_t>(j) * ld;
+  Real ss = 0;
+  for (int k = j + 1 + lane; k < cols; k += 32) ss = fma(row[k], row[k], ss);
+  ss = warp_sum(ss);
+  const Real alpha = row[j];
+  Real beta = alpha, t = 0, scale = 1;
+  if (ss != Real(0)) {
+    beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
+    t = (beta - alpha) / beta;
+    scale = Real(1) / (alpha - beta);
+  }
+  for (int k = j + 1 + lane; k < cols; k += 32) row[k] *= scale;
+  __syncwarp();
+  if (lane == 0) {
+    row[j] = 1;
+    tau[j] = t;
+    if (rdiag != nullptr) {
+      rdiag[j] = Real(1) / beta;
+      if (!(fabs(beta) > Real(0)) || !isfinite(beta)) atomicOr(status, kStatusNumeric);
+    }
+  }
+}
+
+// In-place Householder LQ of M (rows x cols, rows <= cols, leading dimension ld).
+template <class Real>
+__device__ void lq_factor(Real* M, int ld, int rows, int cols, Real* tau, Real* rdiag,
+                          int* status) {
+  const int gid = threadIdx.x / G, q = threadIdx.x % G;
+  for (int j = 0; j < rows; ++j) {
+    make_reflector(M, ld, j, cols, tau, rdiag, status);
+    __syncthreads();
+    const Real tj = tau[j];
+    const Real* v = M + static_cast<size_t>(j) * ld;
+    const int remaining = rows - j - 1;
+    for (int base = 0; base < remaining; base += NGROUPS) {
+      const int i = j + 1 + base + gid;
+      const bool active = i < rows;
+      Real* ri = M + static_cast<size_t>(active ? i : j) * ld;
+      Real part = 0;
+      for (int k = j + q; k < cols; k += G) part = fma(ri[k], v[k], part);
+      const Real w = group_sum(part) * tj;
+      if (active)
+        for (int k = j + q; k < cols; k += G) ri[k] = fma(-w, v[k], ri[k]);
+    }
+    __syncthreads();
+  }
+}
+
+// y <- y H_j for the reflector stored in row j of M (columns j..cols-1, leading 1 explicit).
+// Slots wholly left of column j are skipped (warp-uniform); inside the boundary slot the
+// columns k < j select a zero, so every slot costs exactly one FMA per pass.
+template <class Real, int NS>
+__device__ __forceinline__ void apply_reflector(Real (&y)[NS], const Real* v, Real tj, int j,
+                                                int cols, int q) {
+  Real part = 0;
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    if (G * t + G - 1 < j || G * t >= cols) continue;
+    const int k = q + G * t;
+    const Real vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : Real(0);
+    part = fma(y[t], vk, part);
+  }
+  const Real w = group_sum(part) * tj;
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    if (G * t + G - 1 < j || G * t >= cols) continue;
+    const int k = q + G * t;
+    const Real vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : Real(0);
+    y[t] = fma(-w, vk, y[t]);
+  }
+}
+
+// Streams rows [row0, row1) of the sample block S (n x s, leading dimension s) through the n
+// reflectors of the factored test block F. Writes the last r entries of each transformed row
+// to X (n x r, row-major) when X != NULL, and the row of W = S Omega^+ (n x n).
+template <int NS>
+__device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, int row0, int row1,
+                            const double* F, int ldF, const double* tau, const double* rdiag,
+                            double* __restrict__ X, double* __restrict__ W) {
+  const int gid = threadIdx.x / G, q = threadIdx.x % G;
+  const int gbase = (threadIdx.x % 32) & ~(G - 1);
+  for (int base = row0; base < row1; base += NGROUPS) {
+    const int i = base + gid;
+    const bool active = i < row1;
+    double y[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      y[t] = (active && k < s) ? S[static_cast<size_t>(i) * s + k] : 0.0;
+    }
+    for (int j = 0; j < n; ++j)
+      apply_reflector<double, NS>(y, F + static_cast<size_t>(j) * ldF, tau[j], j, s, q);
+    if (X != nullptr && active) {
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int k = q + G * t;
+        if (k >= s - r && k < s) X[static_cast<size_t>(i) * r + (k - (s - r))] = y[t];
+      }
+    }
+    // W L_1 = (y Q)(0:n): column-oriented back substitution, L_1 = lower triangle of F.
+#pragma unroll
+    for (int t = NS - 1; t >= 0; --t) {
+      if (G * t >= n) continue;
+#pragma unroll 1
+      for (int qq = G - 1; qq >= 0; --qq) {
+        const int j = qq + G * t;
+        if (j >= n) continue;
+        const double wj = __shfl_sync(FULL, y[t], gbase + qq) * rdiag[j];
+        if (q == qq) y[t] = wj;
+        const double* Lj = F + static_cast<size_t>(j) * ldF;
+#pragma unroll
+        for (int tt = 0; tt <= t; ++tt) {
+          const int k = q + G * tt;
+          if (k < j) y[tt] = fma(-wj, Lj[k], y[tt]);
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int k = q + G * t;
+        if (k < n) W[static_cast<size_t>(i) * n + k] = y[t];
+      }
+    }
+  }
+}
+
+// Basis B (n x r, leading dimension ldB, FP64 storage) = first r columns of H_0 ... H_{r-1},
+// the reflectors of the LQ of XT (r x n) -- i.e. col(X, r) for X = XT^*.
+template <class Real, int NS>
+__device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int n,
+                           double* __restrict__ B, int ldB) {
+  const int gid = threadIdx.x / G, q = threadIdx.x % G;
+  for (int base = 0; base < r; base += NGROUPS) {
+    const int c = base + gid;
+    const bool active = c < r;
+    Real u[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) u[t] = (q + G * t == c) ? Real(1) : Real(0);
+    const int jmax = min(r, base + NGROUPS) - 1;
+    for (int j = jmax; j >= 0; --j)
+      apply_reflector<Real, NS>(u, XT + static_cast<size_t>(j) * ldX, tau2[j], j, n, q);
+    if (active) {
+#pragma unroll
+      for (int t = 0; t < NS; ++t) {
+        const int k = q + G * t;
+        if (k < n) B[static_cast<size_t>(k) * ldB + c] = static_cast<double>(u[t]);
+      }
+    }
+  }
+}
+
+// ---- side kernel: LQ of one test block, its sample rows -> W rows and X rows (FP64) ---------
+
+template <int NS>
+__global__ void __launch_bounds__(THREADS, 2)
+    node_side(const NodeTask* __restrict__ tasks, int row_splits, int* status) {
+  extern __shared__ double smem[];
+  const NodeTask tk = tasks[blockIdx.x];
+  const int side = blockIdx.y;
+  if (tk.is_root && side == 1) return;                 // the root needs Y Omega^+ only
+  const int n = tk.n, r = tk.r, s = tk.s;
+  const int chunk = (n + row_splits - 1) / row_splits;
+  const int row0 = blockIdx.z * chunk, row1 = min(n, row0 + chunk);
+  if (row0 >= row1) return;
+  const int ldF = s + 1;
+  double* F = smem;                                    // n x ldF
+  double* tau = F + static_cast<size_t>(n) * ldF;      // n
+  double* rdiag = tau + n;                             // n
+  const double* T = side ? tk.Ps : tk.Om;
+  for (int e = threadIdx.x; e < n * s; e += THREADS) F[(e / s) * ldF + e % s] = T[e];
+  __syncthreads();
+  lq_factor<double>(F, ldF, n, s, tau, rdiag, status);
+  if (tk.is_root) {
+    stream_rows<NS>(tk.Y, n, s, 0, row0, row1, F, ldF, tau, rdiag, nullptr, tk.D);
+    return;
+  }
+  stream_rows<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, F, ldF, tau, rdiag,
+                  side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
+}
+
+// ---- finish kernel: bases, D_tau and the parent's blocks, in Real precision ----------------
+
+template <class Real, int NS>
+__global__ void __launch_bounds__(THREADS, 1)
+    node_finish(const NodeTask* __restrict__ tasks, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_bytes[];
+  Real* smem = reinterpret_cast<Real*>(smem_bytes);
+  const NodeTask tk = tasks[blockIdx.x];
+  if (tk.is_root) return;
+  const int n = tk.n, r = tk.r, s = tk.s;
+  const int ldX = n + 1, ldT = n + 1;
+  Real* XT = smem;                                     // r x ldX: sample block of col, later G1
+  Real* T2 = XT + static_cast<size_t>(r) * ldX;        // n x ldT: (I - VV^*) WZ, later D
+  Real* Hs = T2 + static_cast<size_t>(n) * ldT;        // r x n: U^*(T2^* - WY), later (D V)^*
+  Real* tau2 = Hs + static_cast<size_t>(r) * n;        // r
+
+  // ---- U = col(Y P, r), V = col(Z Q, r) ----
+  for (int side = 0; side < 2; ++side) {
+    const double* X = side ? tk.XZ : tk.XY;
+    for (int e = threadIdx.x; e < n * r; e += THREADS)
+      XT[(e % r) * ldX + e / r] = static_cast<Real>(X[e]);
+    __syncthreads();
+    lq_factor<Real>(XT, ldX, r, n, tau2, nullptr, status);
+    form_basis<Real, NS>(XT, ldX, tau2, r, n, side ? tk.V : tk.U, r);
+    __syncthreads();
+  }
+
+  // ---- D_tau (Eq. d_tau_formula); U, V, WY, WZ were written before this point ----
+  const double* U = tk.U;
+  const double* V = tk.V;
+  const double* WY = tk.WY;
+  const double* WZ = tk.WZ;
+  Real* G1 = XT;
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, j = e % n;
+    Real acc = 0;
+    for (int i = 0; i < n; ++i)
+      acc = fma(static_cast<Real>(V[i * r + c]), static_cast<Real>(WZ[static_cast<size_t>(i) * n + j]), acc);
+    G1[c * ldX + j] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += THREADS) {
+    const int i = e / n, j = e % n;
+    Real acc = static_cast<Real>(WZ[e]);
+    for (int c = 0; c < r; ++c) acc = fma(-static_cast<Real>(V[i * r + c]), G1[c * ldX + j], acc);
+    T2[i * ldT + j] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, j = e % n;
+    Real h2 = 0, ky = 0;
+    for (int i = 0; i < n; ++i) {
+      const Real u = static_cast<Real>(U[i * r + c]);
+      h2 = fma(u, T2[j * ldT + i], h2);
+      ky = fma(u, static_cast<Real>(WY[static_cast<size_t>(i) * n + j]), ky);
+    }
+    G1[c * ldX + j] = h2;
+    Hs[c * n + j] = h2 - ky;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += THREADS) {
+    const int i = e / n, j = e % n;
+    Real acc = static_cast<Real>(WY[e]);
+    for (int c = 0; c < r; ++c) acc = fma(static_cast<Real>(U[i * r + c]), Hs[c * n + j], acc);
+    tk.D[e] = static_cast<double>(acc);
+    T2[i * ldT + j] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, i = e % n;
+    Real acc = 0;
+    for (int j = 0; j < n; ++j) acc = fma(T2[i * ldT + j], static_cast<Real>(V[j * r + c]), acc);
+    Hs[c * n + i] = acc;
+  }
+  __syncthreads();
+
+  // ---- this node's rows of the parent's blocks (Eq. omega_tau_and_y_tau) ----
+  for (int e = threadIdx.x; e < r * s; e += THREADS) {
+    const int c = e / s, k = e % s;
+    Real om = 0, ps = 0, y = 0, z = 0;
+    for (int i = 0; i < n; ++i) {
+      const size_t ik = static_cast<size_t>(i) * s + k;
+      const Real u = static_cast<Real>(U[i * r + c]), v = static_cast<Real>(V[i * r + c]);
+      const Real omk = static_cast<Real>(tk.Om[ik]), psk = static_cast<Real>(tk.Ps[ik]);
+      om = fma(v, omk, om);
+      ps = fma(u, psk, ps);
+      y = fma(u, static_cast<Real>(tk.Y[ik]), y);
+      y = fma(-G1[c * ldX + i], omk, y);
+      z = fma(v, static_cast<Real>(tk.Z[ik]), z);
+      z = fma(-Hs[c * n + i], psk, z);
+    }
+    tk.Om_p[e] = static_cast<double>(om);
+    tk.Ps_p[e] = static_cast<double>(ps);
+    tk.Y_p[e] = static_cast<double>(y);
+    tk.Z_p[e] = static_cast<double>(z);
+  }
+}
+
+template <class Kernel>
+cudaError_t allow_smem(Kernel kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kMaxNodeSmemBytes));
+}
+
+}  // namespace
+
+size_t side_smem_doubles(int n, int s) {
+  return static_cast<size_t>(n) * (s + 1) + 2 * static_cast<size_t>(n);
+}
+
+size_t finish_smem_reals(int n, int r) {
+  return static_cast<size_t>(r) * (n + 1) + static_cast<size_t>(n) * (n + 1) +
+         static_cast<size_t>(r) * n + r;
+}
+
+int side_row_splits(int ntasks, int n) {
+  // aim at two CTAs per SM over both sides; keep at least 8 rows per CTA
+  const int want = (2 * 152 + 2 * ntasks - 1) / (2 * ntasks);
+  const int cap = std::max(1, n / 8);
+  return std::max(1, std::min(want, cap));
+}
+
+cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
+                               int max_s, bool fp32_finish, int* d_status, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (max_s > kMaxS) return cudaErrorInvalidValue;
+  const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
+  const size_t fin_bytes = finish_smem_reals(max_n, max_r) * (fp32_finish ? sizeof(float) : sizeof(double));
+  if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
+  const int splits = side_row_splits(ntasks, max_n);
+  const dim3 side_grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
+  cudaError_t e = cudaSuccess;
+  auto side = [&](auto kernel) {
+    e = allow_smem(kernel);
+    if (e == cudaSuccess) {
+      kernel<<<side_grid, THREADS, side_bytes, st>>>(d_tasks, splits, d_status);
+      e = cudaGetLastError();
+    }
+  };
+  auto finish = [&](auto kernel) {
+    e = allow_smem(kernel);
+    if (e == cudaSuccess) {
+      kernel<<<ntasks, THREADS, fin_bytes, st>>>(d_tasks, d_status);
+      e = cudaGetLastError();
+    }
+  };
+  if (max_s <= 8 * G) side(node_side<8>);
+  else if (max_s <= 16 * G) side(node_side<16>);
+  else side(node_side<24>);
+  if (e != cudaSuccess) return e;
+  // the finish kernel's register slots span the n <= s columns of a basis
+  if (fp32_finish) {
+    if (max_n <= 8 * G) finish(node_finish<float, 8>);
+    else if (max_n <= 16 * G) finish(node_finish<float, 16>);
+    else finish(node_finish<float, 24>);
+  } else {
+    if (max_n <= 8 * G) finish(node_finish<double, 8>);
+    else if (max_n <= 16 * G) finish(node_finish<double, 16>);
+    else finish(node_finish<double, 24>);
+  }
+  return e;
+}
+
+}  // namespace hbs

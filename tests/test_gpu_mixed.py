@@ -74,3 +74,63 @@ def test_mixed_rejects_fp64_operator(hb):
     with pytest.raises(hb.HBSError) as e:
         hb.hbs_sample(A, s, 1, *X, precision=2)
     assert e.value.code == -8
+
+
+# ---- the mixed sweep: FP64 nullspace / pseudo-inverse, FP32 bases, D_tau and merges ---------
+
+def _factor_err(hb, h, F, blk, nodes):
+    from oracle.linalg import pinv
+    worst = 0.0
+    for t in nodes:
+        U, V, D = hb.hbs_get_node(h, t)
+        scale = max(np.linalg.norm(F.D[t]), np.linalg.norm(blk["Y"][t] @ pinv(blk["Omega"][t])))
+        worst = max(worst, np.linalg.norm(D.numpy() - F.D[t]) / scale)
+        if t > 1:
+            worst = max(worst, rel(U.numpy(), F.U[t]), rel(V.numpy(), F.V[t]))
+    return worst
+
+
+@pytest.mark.parametrize("N,r,s,leaf", [(1024, 10, 30, 16), (2048, 40, 120, 64), (777, 12, 40, 26)])
+def test_mixed_sweep_random_inputs(hb, N, r, s, leaf):
+    # FP32 arithmetic in the bases, D_tau and the merges: each factor within 5e-5 of the FP64
+    # oracle (FP32 rounding 6e-8 in products of length n <= 120, compounded over up to 7
+    # levels; measured 1e-5 .. 2.2e-5)
+    from oracle.compress import compress as ocompress
+    x = [gaussian((N, s), 31 * N + i) for i in range(4)]
+    F, blk = ocompress(*x, r, leaf, keep_blocks=True)
+    h = hb.hbs_compress([hb.Problem(N, r, s, leaf, *[torch.as_tensor(v, device="cuda") for v in x])],
+                        precision=2)
+    hb.hbs_sync_status(h)
+    assert _factor_err(hb, h, F, blk, range(1, 2 ** (F.L + 1))) <= 5e-5
+
+
+@pytest.mark.parametrize("N,k,r,s,leaf", [(1000, 6, 9, 27, 18), (4096, 8, 12, 36, 24)])
+def test_mixed_pipeline_exact_hbs(hb, N, k, r, s, leaf):
+    # bf16x6 sampling of the FP32-stored matrix plus the mixed sweep, against the same matrix
+    # and against the FP64 oracle run on it (measured 1.2e-5 at N = 4096; bound 5e-5). With the
+    # FP64 sweep instead, only the sampling error (~6e-8) remains: bound 1e-6.
+    from hbs_inputs import exact_hbs
+    from oracle import apply as oapply
+    from oracle.compress import compress as ocompress
+    A32 = exact_hbs(N, leaf, k, 3).dense().astype(np.float32)
+    A = A32.astype(np.float64)
+    lda = (N + 3) // 4 * 4
+    Ad = torch.zeros((N, lda), dtype=torch.float32, device="cuda")[:, :N]
+    Ad.copy_(torch.as_tensor(A32))
+    Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
+    hb.hbs_sample(Ad, s, 9, Om, Ps, Y, Z, precision=2)
+    h = hb.hbs_compress([hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)], precision=2)
+    X = torch.eye(N, dtype=torch.float64, device="cuda")
+    Out = torch.empty_like(X)
+    hb.hbs_apply(h, X, Out)
+    hb.hbs_sync_status(h)
+    At = Out.cpu().numpy()
+    Ao = oapply.dense(ocompress(*osample(A, N, s, 9), r, leaf))
+    assert rel(At, A) <= 5e-5
+    assert rel(At, Ao) <= 5e-5
+    h64 = hb.hbs_compress([hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)], precision=0)
+    hb.hbs_apply(h64, X, Out)
+    hb.hbs_sync_status(h64)
+    At64 = Out.cpu().numpy()
+    assert rel(At64, A) <= 1e-6
+    assert rel(At64, Ao) <= 1e-6
