@@ -4,8 +4,12 @@ Workload (default): dense 2D log kernel A_ij = log|x_i - x_j| (A_ii = 0) on N = 
 evenly spaced in angle on r(theta) = 1 + 0.3 cos 5 theta, rank parameter r = 40, s = 120 test
 vectors, leaf size 64 (the largest power-of-two split with leaf <= s - r), all in FP64.
 A step draws Omega and Psi (Philox, 2 launches), forms Y = A Omega and Z = A^* Psi (2 FP64
-GEMM launches) and runs the sweep (one launch per tree level, 10 levels). A (8.6 GB) is
+GEMM launches) and runs the sweep (two launches per tree level, 10 levels). A (8.6 GB) is
 resident in HBM before timing and is streamed in full every step, so no L2 flush is needed.
+The same run also times the mixed precisions on the same matrix stored in FP32 (``modes``):
+"mixed" (bf16x6 tensor-core products, FP32 node arithmetic around the FP64 nullspace and
+pseudo-inverse) and "tc64" (bf16x6 products, FP64 sweep), each with its accuracy against A
+and against the FP64 result. ``--only MODE`` times one mode (used for profiling).
 
 Metric: compress throughput N*s / T (sample rows x columns consumed per second) with the
 compress time T in ms_per_step. ``e2e`` repeats the step through the same C ABI calls with A in
@@ -35,6 +39,7 @@ SM_COUNT_GB300 = 152
 FP64_DFMA_PER_CLK_PER_SM = 2          # GB300: FP64 at 1/64 of the FP32 rate (1.25 TF nominal)
 FP64_PROBE_TFLOPS = 1.056             # measured DFMA throughput on this GB300 (see profiles/)
 GEMM_TRAFFIC_8192 = 550.9e6           # dram read+write of one sample_gemm_f64 launch, N = 8192
+BF16_TFLOPS_SUSTAINED = 1666.9        # measured dense bf16 peak on this machine's GB300 (sustained)
 
 
 def tree_nodes(N, leaf):
@@ -206,6 +211,17 @@ def run_reference(args, N, r, s, leaf):
 
 # ------------------------------------------------------------------------------------------
 
+MODES = {
+    "fp64": dict(sample=0, sweep=0, a="f64",
+                 what="FP64 products on the FP64 pipe + FP64 sweep"),
+    "mixed": dict(sample=2, sweep=2, a="f32",
+                  what="A stored FP32; bf16x6 products on tcgen05 tensor cores; sweep with FP64 "
+                       "nullspace QR / pseudo-inverse and FP32 bases, D_tau and merges"),
+    "tc64": dict(sample=2, sweep=0, a="f32",
+                 what="A stored FP32; bf16x6 products on tcgen05 tensor cores; FP64 sweep"),
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +229,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hbs", choices=["hbs", "reference"])
     ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--only", choices=sorted(MODES), default=None,
+                    help="time one precision mode only (default: fp64 headline plus the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -224,7 +242,6 @@ def main():
         run_reference(args, N, r, s, leaf)
         return
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -242,50 +259,65 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     stream = torch.cuda.current_stream()
+    modes = [args.only] if args.only else ["fp64", "mixed", "tc64"]
     A = log_kernel_torch(N, "cuda")
+    A32 = A.float() if any(MODES[m]["a"] == "f32" for m in modes) else None
     Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
-    prob = hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)
-    h = hb.hbs_plan([prob])
     L = tree_nodes(N, leaf)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     seed = SEED + 1000 * rank
-
-    def step(i=None, A_op=A):
-        hb.hbs_draw_gaussian(N, s, 0, seed, Om)
-        hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
-        if i is not None:
-            ev[i][0].record(stream)
-        hb.hbs_sample_products(A_op, s, Om, Ps, Y, Z)
-        if i is not None:
-            ev[i][1].record(stream)
-        hb.hbs_execute(h, [prob])
-
-    for _ in range(args.warmup):
-        step()
-    hb.hbs_sync_status(h)
-    barrier()
     visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
     gpu_id = visible[local].strip() if local < len(visible) and visible[local].strip() else local
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(gpu_id) as clk:
+
+    def timed(mode, steps, warmup, sample_clocks):
+        cfg = MODES[mode]
+        Aop = A if cfg["a"] == "f64" else A32
+        prob = hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)
+        h = hb.hbs_plan([prob], precision=cfg["sweep"])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+
+        def step(i=None):
+            hb.hbs_draw_gaussian(N, s, 0, seed, Om)
+            hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
+            if i is not None:
+                ev[i][0].record(stream)
+            hb.hbs_sample_products(Aop, s, Om, Ps, Y, Z, precision=cfg["sample"])
+            if i is not None:
+                ev[i][1].record(stream)
+            hb.hbs_execute(h, [prob])
+
+        for _ in range(warmup):
+            step()
+        hb.hbs_sync_status(h)
+        hb.hbs_sample_sync()
+        barrier()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(gpu_id) if sample_clocks else None
+        if clk:
+            clk.__enter__()
         barrier()
         start.record(stream)
-        for i in range(args.steps):
+        for i in range(steps):
             step(i)
         stop.record(stream)
         barrier()
-    elapsed = start.elapsed_time(stop) / 1e3
-    gemm_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * args.steps)   # per launch
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    hb.hbs_sync_status(h)
-    clocks = clk.summary()
+        if clk:
+            clk.__exit__(None, None, None)
+        hb.hbs_sync_status(h)
+        hb.hbs_sample_sync()
+        elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3)
+        per_launch = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * steps)
+        return dict(h=h, step=step, elapsed=elapsed, per_launch=per_launch,
+                    clocks=clk.summary() if clk else None)
 
-    # accuracy of the compressed operator: 20-step power iteration (Section 5), on the GPU
     def power_norm(apply_B, apply_Bt, steps=20):
         g = torch.Generator(device="cuda").manual_seed(3)
         v = torch.randn((N, 1), dtype=torch.float64, device="cuda", generator=g)
@@ -293,30 +325,47 @@ def main():
             v = apply_Bt(apply_B(v / torch.linalg.norm(v)))
         return float(torch.sqrt(torch.linalg.norm(v)))
 
-    def apply_h(x, trans=False):
+    def apply_h(h, x, trans=False):
         out = torch.empty_like(x)
         hb.hbs_apply(h, x, out, trans=trans)
         return out
 
-    rel_err = None
-    if not args.no_accuracy:
+    results = {}
+    for i, mode in enumerate(modes):
+        results[mode] = timed(mode, args.steps, args.warmup, sample_clocks=(i == 0))
+    head = modes[0]
+    res = results[head]
+    nA = None
+    if not args.no_accuracy:                     # Section 5 accuracy: 20 power steps on B^* B
         nA = power_norm(lambda x: A @ x, lambda x: A.T @ x)
-        nE = power_norm(lambda x: apply_h(x) - A @ x, lambda x: apply_h(x, True) - A.T @ x)
-        rel_err = nE / nA
+        for mode, rr in results.items():
+            h = rr["h"]
+            rr["rel_error"] = power_norm(lambda x: apply_h(h, x) - A @ x,
+                                         lambda x: apply_h(h, x, True) - A.T @ x) / nA
+        if "fp64" in results:
+            h0 = results["fp64"]["h"]
+            n0 = power_norm(lambda x: apply_h(h0, x), lambda x: apply_h(h0, x, True))
+            for mode, rr in results.items():
+                if mode == "fp64":
+                    continue
+                h = rr["h"]
+                rr["vs_fp64"] = power_norm(lambda x: apply_h(h, x) - apply_h(h0, x),
+                                           lambda x: apply_h(h, x, True) - apply_h(h0, x, True)) / n0
 
     # end to end through the C ABI with host buffers: A in, factors out, every step
     e2e = None
     if not args.no_e2e:
-        A_host = torch.empty((N, N), dtype=torch.float64, pin_memory=True)
-        A_host.copy_(A)
+        h = res["h"]
+        cfg = MODES[head]
+        src = A if cfg["a"] == "f64" else A32
+        A_host = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
+        A_host.copy_(src)
         F_host = torch.empty(hb.hbs_factor_bytes(h), dtype=torch.uint8, pin_memory=True)
-        A_dev2 = torch.empty_like(A)
-        del A
-        torch.cuda.empty_cache()
+        dst = src                                   # the device copy the step multiplies
 
         def e2e_step():
-            A_dev2.copy_(A_host, non_blocking=True)
-            step(None, A_dev2)
+            dst.copy_(A_host, non_blocking=True)
+            res["step"]()
             hb.hbs_copy_factors(h, F_host)
 
         e2e_step()
@@ -327,38 +376,52 @@ def main():
             e2e_step()
         e1.record(stream)
         barrier()
-        te = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3)
         e2e = {"value": world * N * s * args.steps / te, "unit": UNIT,
-               "h2d_bytes_per_step": N * N * 8, "d2h_bytes_per_step": hb.hbs_factor_bytes(h)}
+               "h2d_bytes_per_step": src.numel() * src.element_size(),
+               "d2h_bytes_per_step": hb.hbs_factor_bytes(h)}
 
-    value = world * N * s * args.steps / elapsed
-    flops_gemm = 2.0 * N * N * s                            # one of the two products
-    fp64_peak = SM_COUNT_GB300 * FP64_DFMA_PER_CLK_PER_SM * 2 * 2070e6 / 1e12
-    achieved = flops_gemm / gemm_s / 1e12
+    value = world * N * s * args.steps / res["elapsed"]
+    flops_product = 2.0 * N * N * s                          # one of the two products
+    if MODES[head]["sample"] == 0:
+        peak = SM_COUNT_GB300 * FP64_DFMA_PER_CLK_PER_SM * 2 * 2070e6 / 1e12
+        achieved = flops_product / res["per_launch"] / 1e12
+        roofline = {"kernel": "sample_gemm_f64 (Y = A Omega, Z = A^T Psi)", "bound": "alu",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": GEMM_TRAFFIC_8192 * (N / 8192) ** 2,
+                    "traffic_source": "ncu capture at N=8192 scaled by (N/8192)^2",
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
+                    "probe_peak": FP64_PROBE_TFLOPS}
+    else:
+        peak = BF16_TFLOPS_SUSTAINED
+        achieved = 6 * flops_product / res["per_launch"] / 1e12
+        roofline = {"kernel": "sliced_gemm_tc (bf16x6: 6 slice products per FP32 product)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"log-kernel N={N} r={r} s={s} leaf={leaf} FP64 dense",
-                   "N": N, "r": r, "s": s, "leaf": leaf, "levels": L + 1, "precision": "fp64",
-                   "l2": "inputs larger than L2 (A = %.1f GB streamed every step)" % (N * N * 8 / 1e9),
+        "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if head == "fp64" else "bf16x6/f32/f64", "data": "synthetic",
+        "config": {"workload": f"log-kernel N={N} r={r} s={s} leaf={leaf} dense",
+                   "N": N, "r": r, "s": s, "leaf": leaf, "levels": L + 1, "mode": head,
+                   "precision": MODES[head]["what"],
+                   "l2": "inputs larger than L2 (A is %.1f GB, streamed every step)"
+                         % (A.numel() * A.element_size() / 1e9),
                    "parallelism": f"replicas x{world}"},
-        "rel_error": {"opnorm_power20": rel_err, "vs": "dense A"},
-        "compress_ms": elapsed / args.steps * 1e3,
+        "rel_error": {"opnorm_power20": res.get("rel_error"), "vs": "dense A"},
+        "compress_ms": res["elapsed"] / args.steps * 1e3,
         "sweep_gflop": sweep_flops(N, r, s, leaf) / 1e9,
-        "gpu_launches": args.steps * (2 + 2 + (L + 1)),
-        "roofline": {"kernel": "sample_gemm_f64 (Y = A Omega, Z = A^T Psi)", "bound": "alu",
-                     "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": GEMM_TRAFFIC_8192 * (N / 8192) ** 2,
-                     "traffic_source": "ncu capture at N=8192 scaled by (N/8192)^2",
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
-                     "probe_peak": FP64_PROBE_TFLOPS},
-        "clocks": clocks,
+        "gpu_launches": args.steps * ((2 + 2 + 2 * (L + 1)) if MODES[head]["sample"] == 0
+                                      else (2 + 6 + 2 * (L + 1))),
+        "roofline": roofline,
+        "clocks": res["clocks"],
+        "modes": {m: {"ms_per_step": rr["elapsed"] / args.steps * 1e3,
+                      "value": world * N * s * args.steps / rr["elapsed"],
+                      "rel_error": rr.get("rel_error"), "vs_fp64": rr.get("vs_fp64"),
+                      "products_ms_per_launch": rr["per_launch"] * 1e3,
+                      "what": MODES[m]["what"]} for m, rr in results.items()},
     }
     if e2e:
         line["e2e"] = e2e
@@ -366,7 +429,8 @@ def main():
         t_cpu, sample = oracle_sample_time(N, r, s, leaf)
         line["cpu_baseline"] = {"value": N * s / t_cpu, "unit": UNIT, "cores": cpu_cores(),
                                 "kind": "oracle", "sample": sample}
-    h.free()
+    for rr in results.values():
+        rr["h"].free()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

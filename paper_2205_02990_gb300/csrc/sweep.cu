@@ -343,6 +343,132 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// FP32 finish with every operand staged in shared memory once. On GB300 a conversion from FP64
+// runs at the FP64 rate, so converting each operand inside the product loops (one conversion per
+// FMA) would make this kernel as slow as its FP64 twin; staged, a node converts each input entry
+// once (4 n s + 2 n^2 + 2 n r values) and the loops run on FP32 data in shared memory.
+template <int NS>
+__global__ void __launch_bounds__(THREADS, 1)
+    node_finish_f32(const NodeTask* __restrict__ tasks, int* status) {
+  extern __shared__ __align__(16) float fsm[];
+  const NodeTask tk = tasks[blockIdx.x];
+  if (tk.is_root) return;
+  const int n = tk.n, r = tk.r, s = tk.s;
+  const int ldX = n + 1, ldT = n + 1;
+  float* XT = fsm;                                     // r x ldX: col sample block, later G1 = U^* T2^*
+  float* Hs = XT + static_cast<size_t>(r) * ldX;       // r x n: U^*(T2^* - WY), later (D V)^*
+  float* tau2 = Hs + static_cast<size_t>(r) * n;       // r
+  float* Us = tau2 + r;                                // n x r
+  float* Vs = Us + static_cast<size_t>(n) * r;         // n x r
+  float* T2 = Vs + static_cast<size_t>(n) * r;         // n x ldT: (I - VV^*) WZ, later D
+  float* WYs = T2 + static_cast<size_t>(n) * ldT;      // n x n
+  float* WZs = WYs + static_cast<size_t>(n) * n;       // n x n
+  float* free0 = T2;                                   // staging area for the merge blocks
+  const size_t free_floats = static_cast<size_t>(n) * ldT + 2 * static_cast<size_t>(n) * n;
+
+  // ---- U = col(Y P, r), V = col(Z Q, r), kept in shared memory (and stored as FP64) ----
+  for (int side = 0; side < 2; ++side) {
+    const double* X = side ? tk.XZ : tk.XY;
+    for (int e = threadIdx.x; e < n * r; e += THREADS)
+      XT[(e % r) * ldX + e / r] = static_cast<float>(X[e]);
+    __syncthreads();
+    lq_factor<float>(XT, ldX, r, n, tau2, nullptr, status);
+    double* B = side ? tk.V : tk.U;
+    form_basis<float, NS>(XT, ldX, tau2, r, n, B, r);
+    __syncthreads();
+    float* Bs = side ? Vs : Us;
+    for (int e = threadIdx.x; e < n * r; e += THREADS) Bs[e] = static_cast<float>(B[e]);
+  }
+  for (int e = threadIdx.x; e < n * n; e += THREADS) {
+    WYs[e] = static_cast<float>(tk.WY[e]);
+    WZs[e] = static_cast<float>(tk.WZ[e]);
+  }
+  __syncthreads();
+
+  // ---- D_tau (Eq. d_tau_formula) ----
+  float* G1 = XT;
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, j = e % n;
+    float acc = 0.f;
+    for (int i = 0; i < n; ++i) acc = fmaf(Vs[i * r + c], WZs[i * n + j], acc);
+    G1[c * ldX + j] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += THREADS) {
+    const int i = e / n, j = e % n;
+    float acc = WZs[e];
+    for (int c = 0; c < r; ++c) acc = fmaf(-Vs[i * r + c], G1[c * ldX + j], acc);
+    T2[i * ldT + j] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, j = e % n;
+    float h2 = 0.f, ky = 0.f;
+    for (int i = 0; i < n; ++i) {
+      const float u = Us[i * r + c];
+      h2 = fmaf(u, T2[j * ldT + i], h2);
+      ky = fmaf(u, WYs[i * n + j], ky);
+    }
+    G1[c * ldX + j] = h2;
+    Hs[c * n + j] = h2 - ky;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += THREADS) {
+    const int i = e / n, j = e % n;
+    float acc = WYs[e];
+    for (int c = 0; c < r; ++c) acc = fmaf(Us[i * r + c], Hs[c * n + j], acc);
+    tk.D[e] = static_cast<double>(acc);
+    T2[i * ldT + j] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, i = e % n;
+    float acc = 0.f;
+    for (int j = 0; j < n; ++j) acc = fmaf(T2[i * ldT + j], Vs[j * r + c], acc);
+    Hs[c * n + i] = acc;
+  }
+  __syncthreads();
+
+  // ---- this node's rows of the parent's blocks, in column chunks staged as FP32 ----
+  // pass 0: Omega_p = V^* Omega_tau, Y_p = U^* Y_tau - (U^* D) Omega_tau
+  // pass 1: Psi_p = U^* Psi_tau,     Z_p = V^* Z_tau - (D V)^* Psi_tau
+  const int kc = static_cast<int>(min(static_cast<size_t>(s), free_floats / (2 * static_cast<size_t>(n))));
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* T = pass ? tk.Ps : tk.Om;
+    const double* S = pass ? tk.Z : tk.Y;
+    const float* Bt = pass ? Us : Vs;                  // basis reducing the test block
+    const float* Bs = pass ? Vs : Us;                  // basis reducing the sample block
+    const float* Hm = pass ? Hs : G1;                  // U^* D or (D V)^*
+    const int ldH = pass ? n : ldX;
+    double* outT = pass ? tk.Ps_p : tk.Om_p;
+    double* outS = pass ? tk.Z_p : tk.Y_p;
+    for (int k0 = 0; k0 < s; k0 += kc) {
+      const int kw = min(kc, s - k0);
+      float* Ts = free0;                               // n x kw
+      float* Ss = free0 + static_cast<size_t>(n) * kw; // n x kw
+      __syncthreads();
+      for (int e = threadIdx.x; e < n * kw; e += THREADS) {
+        const int i = e / kw, k = e % kw;
+        Ts[e] = static_cast<float>(T[static_cast<size_t>(i) * s + k0 + k]);
+        Ss[e] = static_cast<float>(S[static_cast<size_t>(i) * s + k0 + k]);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < r * kw; e += THREADS) {
+        const int c = e / kw, k = e % kw;
+        float t = 0.f, y = 0.f;
+        for (int i = 0; i < n; ++i) {
+          const float tv = Ts[i * kw + k];
+          t = fmaf(Bt[i * r + c], tv, t);
+          y = fmaf(Bs[i * r + c], Ss[i * kw + k], y);
+          y = fmaf(-Hm[c * ldH + i], tv, y);
+        }
+        outT[c * s + k0 + k] = static_cast<double>(t);
+        outS[c * s + k0 + k] = static_cast<double>(y);
+      }
+    }
+  }
+}
+
 template <class Kernel>
 cudaError_t allow_smem(Kernel kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -360,9 +486,15 @@ size_t finish_smem_reals(int n, int r) {
          static_cast<size_t>(r) * n + r;
 }
 
+// FP32 finish: the FP64 finish's regions plus the staged U, V, WY, WZ (floats).
+size_t finish_f32_smem_floats(int n, int r) {
+  return finish_smem_reals(n, r) + 2 * static_cast<size_t>(n) * r + 2 * static_cast<size_t>(n) * n;
+}
+
 int side_row_splits(int ntasks, int n) {
-  // aim at two CTAs per SM over both sides; keep at least 8 rows per CTA
-  const int want = (2 * 152 + 2 * ntasks - 1) / (2 * ntasks);
+  // fill at most one wave of two CTAs per SM over both sides (every split refactors the test
+  // block, so a second partial wave costs more than it saves); keep at least 8 rows per CTA
+  const int want = (2 * 152) / (2 * ntasks);
   const int cap = std::max(1, n / 8);
   return std::max(1, std::min(want, cap));
 }
@@ -372,7 +504,8 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   if (ntasks <= 0) return cudaSuccess;
   if (max_s > kMaxS) return cudaErrorInvalidValue;
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
-  const size_t fin_bytes = finish_smem_reals(max_n, max_r) * (fp32_finish ? sizeof(float) : sizeof(double));
+  const size_t fin_bytes = fp32_finish ? finish_f32_smem_floats(max_n, max_r) * sizeof(float)
+                                       : finish_smem_reals(max_n, max_r) * sizeof(double);
   if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
   const int splits = side_row_splits(ntasks, max_n);
   const dim3 side_grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
@@ -397,9 +530,9 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   if (e != cudaSuccess) return e;
   // the finish kernel's register slots span the n <= s columns of a basis
   if (fp32_finish) {
-    if (max_n <= 8 * G) finish(node_finish<float, 8>);
-    else if (max_n <= 16 * G) finish(node_finish<float, 16>);
-    else finish(node_finish<float, 24>);
+    if (max_n <= 8 * G) finish(node_finish_f32<8>);
+    else if (max_n <= 16 * G) finish(node_finish_f32<16>);
+    else finish(node_finish_f32<24>);
   } else {
     if (max_n <= 8 * G) finish(node_finish<double, 8>);
     else if (max_n <= 16 * G) finish(node_finish<double, 16>);
