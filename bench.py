@@ -222,6 +222,85 @@ MODES = {
 }
 
 
+def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
+    """256 independent exact-HBS operators (N in {2048, 4096, 8192, 16384}, block rank k in
+    [8, 32]) compressed with r = k + 5 (Section 4: r = k + p, p = 5 usually suffices; with p = 0
+    the method amplifies rounding ~1e7-fold), s = 3r, leaf = largest power of two <= 2r, applied
+    as black boxes (their
+    telescoping factors loaded into a handle, applied by Algorithm 1), sampled by one batched
+    apply per direction, then compressed as one batch: one side and one finish launch per tree
+    height for all 256 trees, replayed from a CUDA graph, row slicing autotuned. Returns timings
+    of the sweep alone (T2) and of drawing + black-box sampling + sweep (T1), FP64 and mixed."""
+    import numpy as np
+    from hbs_inputs import exact_hbs_packed_torch
+    rng = np.random.default_rng(seed)
+    Ns = rng.choice([2048, 4096, 8192, 16384], size=items)
+    ks = rng.integers(8, 33, size=items)
+    probs, gprobs, Oms, Pss, Ys, Zs, packed = [], [], [], [], [], [], []
+    for i in range(items):
+        N, k = int(Ns[i]), int(ks[i])
+        r = k + 5
+        leaf = 1 << int(np.floor(np.log2(2 * r)))
+        s = 3 * r
+        bufs = [torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4)]
+        Oms.append(bufs[0]), Pss.append(bufs[1]), Ys.append(bufs[2]), Zs.append(bufs[3])
+        probs.append(hb.Problem(N, r, s, leaf, *bufs))
+        gprobs.append(hb.Problem(N, k, s, leaf, *bufs))
+        packed.append(exact_hbs_packed_torch(N, leaf, k, seed + i, "cuda"))
+    gen = hb.hbs_plan(gprobs)                          # the black boxes: generator factors
+    hb.hbs_load_factors(gen, torch.cat(packed))
+    del packed
+    total_ns = float(sum(int(p.N) * int(p.s) for p in probs))
+
+    def draw_and_sample():
+        for i, p in enumerate(probs):
+            hb.hbs_draw_gaussian(p.N, p.s, 0, seed + 7 * i, Oms[i])
+            hb.hbs_draw_gaussian(p.N, p.s, 1, seed + 7 * i, Pss[i])
+        hb.hbs_apply_batch(gen, Oms, Ys)
+        hb.hbs_apply_batch(gen, Pss, Zs, trans=True)
+
+    draw_and_sample()
+    out = {"items": items, "total_N_s": total_ns,
+           "shapes": "N in {2048,4096,8192,16384}, k in [8,32], r=k+5, s=3r, leaf=pow2<=2r",
+           "heights": None}
+    for name, prec in (("fp64", 0), ("mixed", 2)):
+        h = hb.hbs_plan(probs, precision=prec)
+        hb.hbs_execute(h, probs)
+        hb.hbs_autotune(h)
+        hb.hbs_execute(h, probs)                       # graph captured with the tuned slicing
+        hb.hbs_sync_status(h)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        for _ in range(reps):
+            hb.hbs_execute(h, probs)
+        e[1].record()
+        e[2].record()
+        for _ in range(reps):
+            draw_and_sample()
+            hb.hbs_execute(h, probs)
+        e[3].record()
+        torch.cuda.synchronize()
+        hb.hbs_sync_status(h)
+        t2 = e[0].elapsed_time(e[1]) / reps
+        t1 = e[2].elapsed_time(e[3]) / reps
+        # accuracy: one probe column per operator, ||(A~ - A) x|| / ||A x|| with A the black box
+        xs = [torch.randn((p.N, 1), dtype=torch.float64, device="cuda") for p in probs]
+        ya = [torch.empty_like(x) for x in xs]
+        yb = [torch.empty_like(x) for x in xs]
+        hb.hbs_apply_batch(gen, xs, ya)
+        hb.hbs_apply_batch(h, xs, yb)
+        errs = [float(torch.linalg.norm(b - a) / torch.linalg.norm(a)) for a, b in zip(ya, yb)]
+        out["heights"] = len(hb.hbs_get_tuning(h))
+        out[name] = {"T2_sweep_ms": t2, "T1_total_ms": t1, "value_T2": total_ns / (t2 / 1e3),
+                     "value_T1": total_ns / (t1 / 1e3), "rel_error_probe_max": max(errs),
+                     "rel_error_probe_median": float(np.median(errs)),
+                     "tuned_row_slices": hb.hbs_get_tuning(h)}
+        h.free()
+    gen.free()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -234,6 +313,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     N, r, s, leaf = args.N, R_DEF, S_DEF, LEAF_DEF
     if args.warmup < 3:
@@ -425,6 +505,13 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.only and not args.no_batched:
+        for rr in results.values():
+            rr["h"].free()
+        results = {}
+        del A, A32
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(hb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, sample = oracle_sample_time(N, r, s, leaf)
         line["cpu_baseline"] = {"value": N * s / t_cpu, "unit": UNIT, "cores": cpu_cores(),

@@ -23,8 +23,10 @@ The tree used by ``exact_hbs`` is the one of Section 3.1 (ceil split, split whil
 larger than the leaf threshold); it is rebuilt here from that description.
 """
 
-from .generators import (CurvePoints, ExactHBS, curve_points, exact_hbs, gaussian,
-                         log_kernel, log_kernel_rows, log_kernel_torch, seed_for)
+from .generators import (CurvePoints, ExactHBS, curve_points, exact_hbs, exact_hbs_packed_torch,
+                         gaussian, log_kernel, log_kernel_rows, log_kernel_torch, pack_telescoping,
+                         packed_layout, seed_for)
 
-__all__ = ["CurvePoints", "ExactHBS", "curve_points", "exact_hbs", "gaussian", "log_kernel",
-           "log_kernel_rows", "log_kernel_torch", "seed_for"]
+__all__ = ["CurvePoints", "ExactHBS", "curve_points", "exact_hbs", "exact_hbs_packed_torch",
+           "gaussian", "log_kernel", "log_kernel_rows", "log_kernel_torch", "pack_telescoping",
+           "packed_layout", "seed_for"]

@@ -165,3 +165,77 @@ def exact_hbs(N, leaf_max, k, seed):
         Dt[k:, :k] = g.B[(b, a)]
         g.D[t] = Dt
     return g
+
+
+def packed_layout(N, leaf_max, r):
+    """Node sizes and offsets (in doubles) of the packed telescoping-factor order used by the
+    library's factor load/copy calls: per node id 1 .., U (n x r) and V (n x r) for nodes below the
+    root, then D (n x n). Returns (L, {node: (offU, offV, offD, n)}, total)."""
+    L, offsets, sizes = _tree(N, leaf_max)
+    out, cur = {}, 0
+    for t in range(1, 2 ** (L + 1)):
+        level = t.bit_length() - 1
+        n = N if L == 0 else (sizes[t] if level == L else 2 * r)
+        oU = oV = None
+        if t > 1:
+            oU, oV = cur, cur + n * r
+            cur += 2 * n * r
+        out[t] = (oU, oV, cur, n)
+        cur += n * n
+    return L, out, cur
+
+
+def pack_telescoping(g):
+    """The generator's telescoping factors (U, V, D per node, Section 3.3) in the packed order."""
+    L, lay, total = packed_layout(g.N, max(g.sizes[2 ** g.L: 2 ** (g.L + 1)]) if g.L else g.N, g.k)
+    flat = np.zeros(total)
+    for t, (oU, oV, oD, n) in lay.items():
+        if oU is not None:
+            flat[oU:oU + n * g.k] = g.U[t].ravel()
+            flat[oV:oV + n * g.k] = g.V[t].ravel()
+        flat[oD:oD + n * n] = g.D[t].ravel()
+    return flat
+
+
+def exact_hbs_packed_torch(N, leaf_max, k, seed, device):
+    """Packed telescoping factors of a random exact-rank HBS matrix (same construction as
+    ``exact_hbs``: orthonormal leaf and parent bases, Gaussian couplings and leaf blocks), drawn
+    with torch on ``device`` for sizes where the dense matrix cannot be formed. Needs equal leaf
+    sizes (N a multiple of 2^L)."""
+    import torch
+    L, lay, total = packed_layout(N, leaf_max, k)
+    out = torch.zeros(total, dtype=torch.float64, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+
+    def gauss(*shape):
+        return torch.randn(*shape, dtype=torch.float64, device=device, generator=gen)
+
+    def orth(cnt, n):
+        q, _ = torch.linalg.qr(gauss(cnt, n, k))
+        return q
+
+    if L == 0:
+        out[:] = gauss(N * N)
+        return out
+    m = N >> L
+    if m << L != N:
+        raise ValueError("exact_hbs_packed_torch needs N divisible by 2^L")
+    for level in range(0, L + 1):
+        cnt = 1 << level
+        first = lay[cnt]
+        start = first[0] if first[0] is not None else first[2]
+        n = first[3]
+        blk = (2 * n * k if level > 0 else 0) + n * n
+        view = out[start:start + cnt * blk].view(cnt, blk)
+        if level > 0:
+            view[:, :n * k] = orth(cnt, n).reshape(cnt, n * k)
+            view[:, n * k:2 * n * k] = orth(cnt, n).reshape(cnt, n * k)
+        if level == L:
+            view[:, blk - n * n:] = gauss(cnt, n * n)
+        else:
+            D = torch.zeros(cnt, 2 * k, 2 * k, dtype=torch.float64, device=device)
+            D[:, :k, k:] = gauss(cnt, k, k)
+            D[:, k:, :k] = gauss(cnt, k, k)
+            view[:, blk - n * n:] = D.reshape(cnt, n * n)
+    return out

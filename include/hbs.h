@@ -164,6 +164,40 @@ int hbs_compress(int32_t batch, const hbs_problem* probs, int32_t precision, hbs
 int hbs_apply(hbs_handle* h, int32_t item, int trans, int32_t ncols, const double* X,
               double* Out, void* cuda_stream);
 
+/* Algorithm 1 for every problem of the handle at once: Out[i] = A~_i X[i] (or A~_i^* X[i]),
+ * X[i], Out[i] device FP64 row-major N_i x ncols[i] (leading dimension ncols[i]); X, Out and
+ * ncols are host arrays with one entry per problem. The upward pass runs one launch per tree
+ * height and the downward pass one per depth across all problems (2 max L + 1 launches). The
+ * handle keeps a workspace (sum over problems of 2 (2^(L+1) - 2) r ncols doubles), grown by
+ * cudaMalloc on the first call that needs more. Errors: HBS_ERR_ARG, HBS_ERR_NOMEM, HBS_ERR_CUDA.
+ */
+int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* const* Out,
+                    const int32_t* ncols, void* cuda_stream);
+
+/* Overwrites every factor of the handle from `src` (host or device), in the order of
+ * hbs_copy_factors: per problem, per node id 1 .. 2^(L+1) - 1, U (n x r) and V (n x r) for nodes
+ * on levels 1..L, then D (n x n; n = 2r at the root, or N when L = 0), all row-major FP64.
+ * This turns any telescoping factorization of Section 3.3 (for instance a known HBS operator to
+ * be used as a black box) into a handle that hbs_apply can apply. Asynchronous on cuda_stream.
+ * Errors: HBS_ERR_ARG, HBS_ERR_CUDA. */
+int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream);
+
+/* Tuning of the sweep launches (Algorithm 2 runs one side and one finish kernel per tree height).
+ * hbs_autotune times the side kernel of every height with 1, 2, 3, 4, 6, 8, 12, 16 row slices
+ * per node (limited to n/8) on the handle's current inputs -- execute the handle once first --
+ * and keeps the fastest; it synchronizes cuda_stream and leaves the factors unchanged.
+ * hbs_get_tuning returns the number of heights in *heights and copies up to `count` slice counts
+ * (0 = automatic) to R (may be NULL); hbs_set_tuning installs saved ones. Errors: HBS_ERR_ARG,
+ * HBS_ERR_CUDA. */
+int hbs_autotune(hbs_handle* h, void* cuda_stream);
+int hbs_get_tuning(const hbs_handle* h, int32_t* R, int32_t count, int32_t* heights);
+int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count);
+
+/* hbs_execute captures the sweep's launches into a CUDA graph the first time it sees a set of
+ * input pointers and replays it afterwards (a stream being captured by the caller gets plain
+ * launches instead). enable = 0 turns this off for the handle. Errors: HBS_ERR_ARG. */
+int hbs_set_graph(hbs_handle* h, int enable);
+
 /* Waits for the handle's queued work (cudaStreamSynchronize on cuda_stream) and returns the
  * device status of its last execution: HBS_OK or HBS_ERR_NUMERIC. Clears the status word. */
 int hbs_sync_status(hbs_handle* h, void* cuda_stream);

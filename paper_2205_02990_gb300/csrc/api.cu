@@ -87,6 +87,7 @@ struct Height {
   std::vector<NodeTask> tasks;
   NodeTask* d_tasks = nullptr;
   int max_n = 0, max_r = 0, max_s = 0;
+  int R = 0;                  // side-kernel row splits (0: automatic, > 0: tuned)
 };
 
 }  // namespace
@@ -104,6 +105,16 @@ struct hbs_handle {
   size_t apply_ws_doubles = 0;
   GemmTask* d_gemm = nullptr;
   size_t d_gemm_cap = 0;
+  std::vector<int> tuned_R;   // per height, kept across task rebuilds
+  // the sweep's launches captured once per set of inputs and replayed
+  bool use_graph = true;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  // hbs_apply_batch workspace and task list
+  double* batch_ws = nullptr;
+  size_t batch_ws_doubles = 0;
+  GemmTask* d_batch = nullptr;
+  size_t d_batch_cap = 0;
 };
 
 namespace {
@@ -142,7 +153,9 @@ int check_problem(const hbs_problem& p, int idx) {
 void build_tasks(hbs_handle* h) {
   int maxL = 0;
   for (auto& it : h->items) maxL = std::max(maxL, it.L);
+  for (auto& H : h->heights) cudaFree(H.d_tasks);
   h->heights.assign(maxL + 1, Height{});
+  for (int t = 0; t <= maxL && t < int(h->tuned_R.size()); ++t) h->heights[t].R = h->tuned_R[t];
   for (auto& it : h->items) {
     const int r = it.r, s = it.s;
     for (int level = it.L; level >= 0; --level) {
@@ -210,7 +223,64 @@ void free_handle(hbs_handle* h) {
   cudaFree(h->d_status);
   cudaFree(h->apply_ws);
   cudaFree(h->d_gemm);
+  cudaFree(h->batch_ws);
+  cudaFree(h->d_batch);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   delete h;
+}
+
+// The sweep's launches, one side and one finish kernel per height, finest height first.
+cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
+  const bool fp32_finish = h->precision != HBS_PREC_FP64;
+  for (auto& H : h->heights) {
+    cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
+                                            H.max_s, fp32_finish, H.R, h->d_status, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Runs the sweep on `st`: replays the captured graph when there is one, else captures the
+// launches on a private stream (so a caller's own capture of `st` is never disturbed) and
+// replays that; launches directly when `st` is itself being captured or capture fails.
+int launch_sweep(hbs_handle* h, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  if (!h->use_graph || cs != cudaStreamCaptureStatusNone) {
+    e = launch_levels(h, st);
+    return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep kernels");
+  }
+  if (!h->graph_exec) {
+    if (!h->capture_stream &&
+        cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      h->capture_stream = nullptr;
+      h->use_graph = false;
+    }
+    cudaGraph_t graph = nullptr;
+    if (h->use_graph &&
+        cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t le = launch_levels(h, h->capture_stream);
+      const cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &graph);
+      if (le != cudaSuccess || ce != cudaSuccess ||
+          cudaGraphInstantiate(&h->graph_exec, graph, 0) != cudaSuccess) {
+        h->graph_exec = nullptr;
+        h->use_graph = false;
+        cudaGetLastError();                       // clear a sticky launch error from capture
+      }
+      if (graph) cudaGraphDestroy(graph);
+    } else {
+      h->use_graph = false;
+      cudaGetLastError();
+    }
+    if (!h->graph_exec) {
+      e = launch_levels(h, st);
+      return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep kernels");
+    }
+  }
+  e = cudaGraphLaunch(h->graph_exec, st);
+  return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep graph launch");
 }
 
 }  // namespace
@@ -404,12 +474,12 @@ int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream) {
     if (rc != HBS_OK) return rc;
     h->tasks_uploaded = true;
   }
-  const bool fp32_finish = h->precision != HBS_PREC_FP64;
-  for (auto& H : h->heights) {
-    cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
-                                            H.max_s, fp32_finish, h->d_status, st);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep kernels");
+  if (changed && h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
   }
+  const int rc = launch_sweep(h, st);
+  if (rc != HBS_OK) return rc;
   return ok();
 }
 
@@ -598,6 +668,194 @@ int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream) {
   cudaError_t e = cudaMemcpyAsync(dst, h->arena, h->factor_doubles * sizeof(double),
                                   cudaMemcpyDefault, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return cuda_fail(e, "hbs_copy_factors");
+  return ok();
+}
+
+int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream) {
+  if (!h || !src) return fail(HBS_ERR_ARG, "hbs_load_factors: bad arguments");
+  cudaError_t e = cudaMemcpyAsync(h->arena, src, h->factor_doubles * sizeof(double),
+                                  cudaMemcpyDefault, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_load_factors");
+  return ok();
+}
+
+int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* const* Out,
+                    const int32_t* ncols, void* cuda_stream) {
+  if (!h || !X || !Out || !ncols) return fail(HBS_ERR_ARG, "hbs_apply_batch: bad arguments");
+  const int nitems = int(h->items.size());
+  int maxL = 0;
+  size_t need = 0;
+  std::vector<size_t> base(nitems);
+  for (int i = 0; i < nitems; ++i) {
+    if (!X[i] || !Out[i] || ncols[i] < 1) return fail(HBS_ERR_ARG, "hbs_apply_batch: item %d", i);
+    const Item& it = h->items[i];
+    maxL = std::max(maxL, it.L);
+    base[i] = need;
+    need += 2 * ((size_t(2) << it.L) - 2) * size_t(it.r) * size_t(ncols[i]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (need > h->batch_ws_doubles) {
+    cudaFree(h->batch_ws);
+    h->batch_ws = nullptr;
+    h->batch_ws_doubles = 0;
+    cudaError_t e = cudaMalloc(&h->batch_ws, std::max<size_t>(need, 1) * sizeof(double));
+    if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "apply workspace: %s", cudaGetErrorString(e));
+    h->batch_ws_doubles = need;
+  }
+  // passes: upward by height (0 = leaves), then downward by depth (0 = root)
+  std::vector<std::vector<GemmTask>> up(std::max(maxL, 1)), down(maxL + 1);
+  const double* A = h->arena;
+  for (int i = 0; i < nitems; ++i) {
+    const Item& it = h->items[i];
+    const int r = it.r, c = ncols[i], L = it.L;
+    double* ws = h->batch_ws + base[i];
+    const size_t half = ((size_t(2) << L) - 2) * size_t(r) * size_t(c);
+    // q-hat / u-hat of node t (levels 1..L) at level-major offsets
+    auto off = [&](int64_t t) {
+      int l = 0;
+      while ((int64_t(2) << l) <= t) ++l;
+      return ((size_t(1) << l) - 2 + size_t(t - (int64_t(1) << l))) * size_t(r) * size_t(c);
+    };
+    auto qhat = [&](int64_t t) { return ws + off(t); };
+    auto uhat = [&](int64_t t) { return ws + half + off(t); };
+    const std::vector<int64_t>& oIn = trans ? it.oU : it.oV;
+    const std::vector<int64_t>& oOut = trans ? it.oV : it.oU;
+    if (L == 0) {
+      GemmTask g{};
+      g.A1 = A + it.oD[1]; g.lda1 = int(it.N); g.t1 = trans; g.k1 = int(it.N);
+      g.B1 = X[i]; g.ldb1 = c; g.C = Out[i]; g.ldc = c; g.m = int(it.N); g.ncols = c;
+      down[0].push_back(g);
+      continue;
+    }
+    for (int l = L; l >= 1; --l) {
+      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
+        GemmTask g{};
+        const int n = int(it.node_rows(t));
+        g.A1 = A + oIn[t]; g.lda1 = r; g.t1 = 1; g.k1 = n; g.m = r; g.ncols = c;
+        g.B1 = (l == L) ? X[i] + it.off[t] * c : qhat(2 * t);
+        g.ldb1 = c; g.C = qhat(t); g.ldc = c;
+        up[L - l].push_back(g);
+      }
+    }
+    for (int l = 0; l <= L; ++l) {
+      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
+        GemmTask g{};
+        g.ncols = c;
+        const int n = (l == 0) ? 2 * r : int(it.node_rows(t));
+        if (l == 0) {
+          g.A1 = A + it.oD[1]; g.lda1 = n; g.t1 = trans; g.k1 = n; g.m = n;
+          g.B1 = qhat(2); g.ldb1 = c; g.C = uhat(2); g.ldc = c;
+        } else {
+          g.A1 = A + oOut[t]; g.lda1 = r; g.t1 = 0; g.k1 = r; g.m = n;
+          g.B1 = uhat(t); g.ldb1 = c;
+          g.A2 = A + it.oD[t]; g.lda2 = n; g.t2 = trans; g.k2 = n;
+          if (l < L) {
+            g.B2 = qhat(2 * t); g.ldb2 = c; g.C = uhat(2 * t); g.ldc = c;
+          } else {
+            g.B2 = X[i] + it.off[t] * c; g.ldb2 = c; g.C = Out[i] + it.off[t] * c; g.ldc = c;
+          }
+        }
+        down[l].push_back(g);
+      }
+    }
+  }
+  std::vector<GemmTask> flat;
+  std::vector<int> sizes;
+  for (auto& p : up) { flat.insert(flat.end(), p.begin(), p.end()); sizes.push_back(int(p.size())); }
+  for (auto& p : down) { flat.insert(flat.end(), p.begin(), p.end()); sizes.push_back(int(p.size())); }
+  if (flat.size() > h->d_batch_cap) {
+    cudaFree(h->d_batch);
+    h->d_batch = nullptr;
+    h->d_batch_cap = 0;
+    cudaError_t e = cudaMalloc(&h->d_batch, flat.size() * sizeof(GemmTask));
+    if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "apply task list: %s", cudaGetErrorString(e));
+    h->d_batch_cap = flat.size();
+  }
+  cudaError_t e = cudaMemcpyAsync(h->d_batch, flat.data(), flat.size() * sizeof(GemmTask),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "apply task upload");
+  size_t at = 0;
+  for (int cnt : sizes) {
+    if (cnt > 0) {
+      e = hbs::launch_gemm_tasks_f64(h->d_batch + at, cnt, 1, st);
+      if (e != cudaSuccess) return cuda_fail(e, "apply kernel");
+    }
+    at += size_t(cnt);
+  }
+  return ok();
+}
+
+int hbs_autotune(hbs_handle* h, void* cuda_stream) {
+  if (!h) return fail(HBS_ERR_ARG, "hbs_autotune: NULL handle");
+  if (!h->tasks_uploaded) return fail(HBS_ERR_ARG, "hbs_autotune: execute the handle once first");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "hbs_autotune: events");
+  h->tuned_R.assign(h->heights.size(), 0);
+  for (size_t t = 0; t < h->heights.size(); ++t) {
+    Height& H = h->heights[t];
+    const int ntasks = int(H.tasks.size());
+    float best_ms = 1e30f;
+    int best = hbs::side_row_splits(ntasks, H.max_n);
+    for (int R : {1, 2, 3, 4, 6, 8, 12, 16}) {
+      if (R > std::max(1, H.max_n / 8)) break;
+      // one untimed launch, then the mean of three
+      cudaError_t e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "hbs_autotune");
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = R;
+      }
+    }
+    H.R = best;
+    h->tuned_R[t] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  return ok();
+}
+
+int hbs_get_tuning(const hbs_handle* h, int32_t* R, int32_t count, int32_t* heights) {
+  if (!h || !heights) return fail(HBS_ERR_ARG, "hbs_get_tuning: bad arguments");
+  *heights = int32_t(h->heights.size());
+  for (int t = 0; R && t < count && t < int(h->heights.size()); ++t) R[t] = h->heights[t].R;
+  return ok();
+}
+
+int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count) {
+  if (!h || !R || count < 0) return fail(HBS_ERR_ARG, "hbs_set_tuning: bad arguments");
+  h->tuned_R.assign(R, R + count);
+  for (int t = 0; t < count && t < int(h->heights.size()); ++t) h->heights[t].R = std::max(0, R[t]);
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  return ok();
+}
+
+int hbs_set_graph(hbs_handle* h, int enable) {
+  if (!h) return fail(HBS_ERR_ARG, "hbs_set_graph: NULL handle");
+  h->use_graph = enable != 0;
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
   return ok();
 }
 

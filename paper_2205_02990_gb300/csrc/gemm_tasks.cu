@@ -11,6 +11,7 @@ constexpr int THREADS = 256;
 __global__ void __launch_bounds__(THREADS) gemm_tasks_f64(const GemmTask* __restrict__ tasks,
                                                           int ncols) {
   const GemmTask t = tasks[blockIdx.x];
+  if (t.ncols > 0) ncols = t.ncols;
   const int total = t.m * ncols;
   for (int e = threadIdx.x; e < total; e += THREADS) {
     const int i = e / ncols, b = e % ncols;

@@ -42,6 +42,7 @@ struct GemmTask {
   int32_t lda1, lda2;
   int32_t ldb1, ldb2, ldc;
   int32_t t1, t2;                       // 1 = transpose
+  int32_t ncols;                        // columns of C and B; 0 = the launch's ncols
 };
 
 // Shared memory of the sweep kernels for a node of n rows (sweep.cu).
@@ -53,7 +54,12 @@ constexpr int kMaxS = 192;              // register tile of the sample-row strea
 // One tree height of Algorithm 2: the side kernel (FP64) then the finish kernel (FP64, or FP32
 // when fp32_finish).
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
-                               int max_s, bool fp32_finish, int* d_status, cudaStream_t st);
+                               int max_s, bool fp32_finish, int row_splits, int* d_status,
+                               cudaStream_t st);
+// The side kernel of one height alone (for tuning its row splits; idempotent).
+cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
+                             int row_splits, int* d_status, cudaStream_t st);
+int side_row_splits(int ntasks, int n);
 cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, double* out,
                             cudaStream_t st);
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,

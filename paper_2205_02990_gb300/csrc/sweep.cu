@@ -499,15 +499,38 @@ int side_row_splits(int ntasks, int n) {
   return std::max(1, std::min(want, cap));
 }
 
+cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
+                             int row_splits, int* d_status, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
+  if (max_s > kMaxS || side_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
+  const int splits = std::max(1, std::min(row_splits, std::max(1, max_n)));
+  const dim3 grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
+  cudaError_t e = cudaSuccess;
+  auto side = [&](auto kernel) {
+    e = allow_smem(kernel);
+    if (e == cudaSuccess) {
+      kernel<<<grid, THREADS, side_bytes, st>>>(d_tasks, splits, d_status);
+      e = cudaGetLastError();
+    }
+  };
+  if (max_s <= 8 * G) side(node_side<8>);
+  else if (max_s <= 16 * G) side(node_side<16>);
+  else side(node_side<24>);
+  return e;
+}
+
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
-                               int max_s, bool fp32_finish, int* d_status, cudaStream_t st) {
+                               int max_s, bool fp32_finish, int row_splits, int* d_status,
+                               cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
   if (max_s > kMaxS) return cudaErrorInvalidValue;
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
   const size_t fin_bytes = fp32_finish ? finish_f32_smem_floats(max_n, max_r) * sizeof(float)
                                        : finish_smem_reals(max_n, max_r) * sizeof(double);
   if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
-  const int splits = side_row_splits(ntasks, max_n);
+  const int splits = row_splits > 0 ? std::max(1, std::min(row_splits, std::max(1, max_n)))
+                                    : side_row_splits(ntasks, max_n);
   const dim3 side_grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
   cudaError_t e = cudaSuccess;
   auto side = [&](auto kernel) {

@@ -33,7 +33,8 @@ HBS_F32 = 1
 EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan", "hbs_execute", "hbs_compress",
             "hbs_apply", "hbs_sync_status", "hbs_free", "hbs_last_error", "hbs_tree",
             "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
-            "hbs_apply_static", "hbs_sample_sync"]
+            "hbs_apply_static", "hbs_sample_sync", "hbs_apply_batch", "hbs_load_factors",
+            "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph"]
 
 
 class HBSError(RuntimeError):
@@ -77,6 +78,12 @@ def load():
         "hbs_sample_products": (c.c_int, [c.POINTER(_Operator), c.c_int32, c.c_int32, c.c_void_p,
                                           c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
         "hbs_sample_sync": (c.c_int, [c.c_void_p]),
+        "hbs_apply_batch": (c.c_int, [c.c_void_p, c.c_int, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+        "hbs_load_factors": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
+        "hbs_autotune": (c.c_int, [c.c_void_p, c.c_void_p]),
+        "hbs_get_tuning": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int32, c.POINTER(c.c_int32)]),
+        "hbs_set_tuning": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int32]),
+        "hbs_set_graph": (c.c_int, [c.c_void_p, c.c_int]),
         "hbs_plan": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p)]),
         "hbs_execute": (c.c_int, [c.c_void_p, c.POINTER(_Problem), c.c_void_p]),
         "hbs_compress": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p),
@@ -279,6 +286,65 @@ def hbs_apply_static(handle, X, Out, item=0, trans=False):
     c = X.shape[1]
     _check(load().hbs_apply_static(handle.ptr, item, int(bool(trans)), c, _dev(X, (N, c), "X"),
                                    _dev(Out, (N, c), "Out"), _stream()))
+
+
+def hbs_apply_batch(handle, Xs, Outs, trans=False):
+    """Algorithm 1 for every problem of the handle: Outs[i] = A~_i Xs[i] (or A~_i^* Xs[i])."""
+    n = len(handle.problems)
+    if len(Xs) != n or len(Outs) != n:
+        raise ValueError("one X and one Out per problem")
+    xp = (ctypes.c_void_p * n)(*[_dev(x, (p.N, x.shape[1]), "X").value for x, p in zip(Xs, handle.problems)])
+    op = (ctypes.c_void_p * n)(*[_dev(o, (p.N, x.shape[1]), "Out").value
+                                 for o, x, p in zip(Outs, Xs, handle.problems)])
+    nc = (ctypes.c_int32 * n)(*[x.shape[1] for x in Xs])
+    _check(load().hbs_apply_batch(handle.ptr, int(bool(trans)), xp, op, nc, _stream()))
+
+
+def hbs_load_factors(handle, src):
+    """Overwrite every factor of the handle from ``src`` (order of hbs_copy_factors)."""
+    if src.numel() * src.element_size() < hbs_factor_bytes(handle):
+        raise ValueError("source too small")
+    _check(load().hbs_load_factors(handle.ptr, ctypes.c_void_p(src.data_ptr()), _stream()))
+
+
+def hbs_autotune(handle):
+    """Time the side kernel's row slicing per tree height on the current inputs; keep the best."""
+    _check(load().hbs_autotune(handle.ptr, _stream()))
+
+
+def hbs_get_tuning(handle):
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib.hbs_get_tuning(handle.ptr, None, 0, ctypes.byref(n)))
+    R = (ctypes.c_int32 * max(n.value, 1))()
+    _check(lib.hbs_get_tuning(handle.ptr, R, n.value, ctypes.byref(n)))
+    return list(R)[:n.value]
+
+
+def hbs_set_tuning(handle, R):
+    arr = (ctypes.c_int32 * max(len(R), 1))(*R)
+    _check(load().hbs_set_tuning(handle.ptr, arr, len(R)))
+
+
+def hbs_set_graph(handle, enable):
+    _check(load().hbs_set_graph(handle.ptr, int(bool(enable))))
+
+
+def factor_layout(N, r, leaf_max):
+    """Offsets (in doubles) of U, V, D per node id in the packed factor order of one problem,
+    and the total length: {node: (offU, offV, offD, n)}, total."""
+    L, off, size = hbs_tree_build(N, leaf_max)
+    out, cur = {}, 0
+    for t in range(1, 2 ** (L + 1)):
+        level = t.bit_length() - 1
+        n = N if L == 0 else (size[t - 1] if level == L else 2 * r)
+        oU = oV = None
+        if t > 1:
+            oU, oV = cur, cur + n * r
+            cur += 2 * n * r
+        out[t] = (oU, oV, cur, n)
+        cur += n * n
+    return out, cur
 
 
 def hbs_sync_status(handle):

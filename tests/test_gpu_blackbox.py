@@ -1,0 +1,170 @@
+"""Black-box operators, batches, graph replay and tuning, through the C ABI.
+
+A known telescoping factorization (the exact-HBS generator of Section 3.2, in the form of
+Section 3.3) is loaded into a handle and applied by Algorithm 1; that handle is then the black
+box (Section 1: A is reachable only through products) for the sampling of Algorithm 2.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from hbs_inputs import exact_hbs, gaussian, pack_telescoping
+from oracle import apply as oapply
+from oracle.compress import compress as ocompress
+from oracle.sample import sample as osample
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_02990_gb300 as hb
+    from paper_2205_02990_gb300 import hbs
+    if not os.path.exists(hbs._LIB_PATH):
+        from paper_2205_02990_gb300.build import build
+        build()
+    hb.load()
+    return hb
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def zeros(N, s):
+    return [torch.zeros((N, s), dtype=torch.float64, device="cuda") for _ in range(4)]
+
+
+def generator_handle(hb, gens, leafs):
+    """Handle holding the generators' telescoping factors (never executed)."""
+    probs = []
+    for g, leaf in zip(gens, leafs):
+        s = max(3 * g.k, (g.sizes[2 ** g.L] if g.L else g.N) + g.k, g.N if g.L == 0 else 0)
+        probs.append(hb.Problem(g.N, g.k, s, leaf, *zeros(g.N, s)))
+    h = hb.hbs_plan(probs)
+    packed = np.concatenate([pack_telescoping(g) for g in gens])
+    hb.hbs_load_factors(h, torch.as_tensor(packed, device="cuda"))
+    return h
+
+
+@pytest.mark.parametrize("N,leaf,k", [(400, 16, 8), (97, 10, 5), (64, 8, 4), (20, 32, 3), (1000, 24, 12)])
+def test_loaded_factors_apply_matches_blockwise_assembly(hb, N, leaf, k):
+    g = exact_hbs(N, leaf, k, 5)
+    A = g.dense()
+    h = generator_handle(hb, [g], [leaf])
+    X = torch.eye(N, dtype=torch.float64, device="cuda")
+    Out = torch.empty_like(X)
+    hb.hbs_apply(h, X, Out)
+    torch.cuda.synchronize()
+    assert rel(Out.cpu().numpy(), A) <= 1e-12
+    hb.hbs_apply(h, X, Out, trans=True)
+    torch.cuda.synchronize()
+    assert rel(Out.cpu().numpy(), A.T) <= 1e-12
+
+
+def test_blackbox_callback_pipeline(hb):
+    # sampling through a callback that applies the generator handle (Section 1 black box)
+    N, k, r, s, leaf, seed = 1000, 6, 9, 27, 18, 21
+    g = exact_hbs(N, leaf, k, 2)
+    A = g.dense()
+    gen = generator_handle(hb, [g], [leaf])
+
+    def op(trans, X, Out):
+        hb.hbs_apply(gen, X, Out, trans=bool(trans))
+
+    Om, Ps, Y, Z = zeros(N, s)
+    hb.hbs_sample(op, s, seed, Om, Ps, Y, Z, N=N)
+    h = hb.hbs_compress([hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)])
+    X = torch.eye(N, dtype=torch.float64, device="cuda")
+    Out = torch.empty_like(X)
+    hb.hbs_apply(h, X, Out)
+    hb.hbs_sync_status(h)
+    At = Out.cpu().numpy()
+    assert rel(At, A) <= 1e-11
+    Ao = oapply.dense(ocompress(*osample(lambda x, t: (A.T if t else A) @ x, N, s, seed), r, leaf))
+    assert rel(At, Ao) <= 1e-10
+
+
+def test_callback_error_is_reported(hb):
+    N, s = 64, 12
+
+    def op(trans, X, Out):
+        raise RuntimeError("operator failed")
+
+    with pytest.raises(hb.HBSError) as e:
+        hb.hbs_sample(op, s, 1, *zeros(N, s), N=N)
+    assert e.value.code == -7
+
+
+def test_batched_blackbox_compression(hb):
+    # several exact-HBS operators of different N and k sampled by one batched apply and
+    # compressed by one launch per tree height
+    shapes = [(1000, 6), (512, 8), (1024, 5), (2048, 10), (256, 4), (1024, 7)]
+    gens, leafs = [], []
+    for j, (N, k) in enumerate(shapes):
+        leaf = 1 << int(np.floor(np.log2(2 * k)))
+        gens.append(exact_hbs(N, leaf, k, 40 + j))
+        leafs.append(leaf)
+    gen = generator_handle(hb, gens, leafs)
+    Oms, Pss, Ys, Zs, probs = [], [], [], [], []
+    for j, (g, leaf) in enumerate(zip(gens, leafs)):
+        r = min(g.k + 2, min(g.sizes[2 ** g.L: 2 ** (g.L + 1)]))      # r = k + p, at most a leaf
+        s = 3 * r
+        Om, Ps, Y, Z = zeros(g.N, s)
+        hb.hbs_draw_gaussian(g.N, s, 0, 100 + j, Om)
+        hb.hbs_draw_gaussian(g.N, s, 1, 100 + j, Ps)
+        Oms.append(Om), Pss.append(Ps), Ys.append(Y), Zs.append(Z)
+        probs.append(hb.Problem(g.N, r, s, leaf, Om, Ps, Y, Z))
+    hb.hbs_apply_batch(gen, Oms, Ys)
+    hb.hbs_apply_batch(gen, Pss, Zs, trans=True)
+    for j, g in enumerate(gens):                       # batched apply = per-item apply
+        ref = torch.empty_like(Ys[j])
+        hb.hbs_apply(gen, Oms[j], ref, item=j)
+        torch.cuda.synchronize()
+        assert torch.equal(ref, Ys[j])
+    h = hb.hbs_compress(probs)
+    hb.hbs_sync_status(h)
+    for j, g in enumerate(gens):
+        X = torch.eye(g.N, dtype=torch.float64, device="cuda")
+        Out = torch.empty_like(X)
+        hb.hbs_apply(h, X, Out, item=j)
+        torch.cuda.synchronize()
+        assert rel(Out.cpu().numpy(), g.dense()) <= 1e-11, j
+
+
+def test_graph_replay_and_tuning_change_nothing(hb):
+    N, r, s, leaf = 2048, 40, 120, 64
+    x = [torch.as_tensor(gaussian((N, s), 60 + i), device="cuda") for i in range(4)]
+    prob = hb.Problem(N, r, s, leaf, *x)
+    h = hb.hbs_plan([prob])
+
+    def factors():
+        hb.hbs_sync_status(h)
+        return [hb.hbs_get_node(h, t)[2] for t in (1, 2, 17, 40, 63)]
+
+    hb.hbs_execute(h, [prob])                          # captures the graph
+    ref = factors()
+    hb.hbs_execute(h, [prob])                          # replays it
+    for a, b in zip(ref, factors()):
+        assert torch.equal(a, b)
+    hb.hbs_set_graph(h, False)
+    hb.hbs_execute(h, [prob])                          # plain launches
+    for a, b in zip(ref, factors()):
+        assert torch.equal(a, b)
+    hb.hbs_set_graph(h, True)
+    hb.hbs_autotune(h)
+    R = hb.hbs_get_tuning(h)
+    assert len(R) == 6 and all(v >= 1 for v in R)
+    hb.hbs_execute(h, [prob])                          # row slicing never changes the arithmetic
+    for a, b in zip(ref, factors()):
+        assert torch.equal(a, b)
+    hb.hbs_set_tuning(h, [1] * len(R))
+    hb.hbs_execute(h, [prob])
+    for a, b in zip(ref, factors()):
+        assert torch.equal(a, b)
