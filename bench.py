@@ -301,6 +301,63 @@ def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
     return out
 
 
+def run_scaling(hb, torch, logN_list, k=45, r=50, s=150, leaf=64, seed=SEED + 500, reps=2):
+    """Linear-complexity check (Section 4.4, Section 5 summary): an exact-HBS operator of block
+    rank k = 45 (N = 2^16 .. 2^22, leaf 64) applied as a black box by Algorithm 1 on its loaded
+    telescoping factors, never formed densely; compressed with r = 50 = k + 5, s = 150 in FP64
+    and in the mixed precision. Per N: sweep time (T2), draw + black-box sampling + sweep (T1),
+    and the accuracy against the operator on 4 random probe columns."""
+    from hbs_inputs import exact_hbs_packed_torch
+    rows = []
+    for logN in logN_list:
+        N = 1 << logN
+        bufs = [torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4)]
+        Om, Ps, Y, Z = bufs
+        prob = hb.Problem(N, r, s, leaf, *bufs)
+        gen = hb.hbs_plan([hb.Problem(N, k, s, leaf, *bufs)])
+        hb.hbs_load_factors(gen, exact_hbs_packed_torch(N, leaf, k, seed + logN, "cuda"))
+
+        def draw_and_sample():
+            hb.hbs_draw_gaussian(N, s, 0, seed, Om)
+            hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
+            hb.hbs_apply(gen, Om, Y)
+            hb.hbs_apply(gen, Ps, Z, trans=True)
+
+        draw_and_sample()
+        row = {"N": N}
+        for name, prec in (("fp64", 0), ("mixed", 2)):
+            h = hb.hbs_plan([prob], precision=prec)
+            hb.hbs_execute(h, [prob])
+            hb.hbs_sync_status(h)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            torch.cuda.synchronize()
+            e[0].record()
+            for _ in range(reps):
+                hb.hbs_execute(h, [prob])
+            e[1].record()
+            e[2].record()
+            for _ in range(reps):
+                draw_and_sample()
+                hb.hbs_execute(h, [prob])
+            e[3].record()
+            torch.cuda.synchronize()
+            hb.hbs_sync_status(h)
+            x = torch.randn((N, 4), dtype=torch.float64, device="cuda")
+            ya, yb = torch.empty_like(x), torch.empty_like(x)
+            hb.hbs_apply(gen, x, ya)
+            hb.hbs_apply(h, x, yb)
+            t2 = e[0].elapsed_time(e[1]) / reps
+            t1 = e[2].elapsed_time(e[3]) / reps
+            row[name] = {"T2_sweep_ms": t2, "T1_total_ms": t1, "ns_per_index_T2": t2 * 1e6 / N,
+                         "rel_error_probe": float(torch.linalg.norm(yb - ya) / torch.linalg.norm(ya))}
+            h.free()
+        gen.free()
+        del bufs, Om, Ps, Y, Z
+        torch.cuda.empty_cache()
+        rows.append(row)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,6 +371,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--workload", default="logkernel", choices=["logkernel", "scaling"],
+                    help="logkernel: the timed N = 32768 log-kernel step (default); scaling: "
+                         "black-box exact-HBS compression for N = 2^16 .. 2^22")
+    ap.add_argument("--max-logN", type=int, default=22)
     args = ap.parse_args()
     N, r, s, leaf = args.N, R_DEF, S_DEF, LEAF_DEF
     if args.warmup < 3:
@@ -333,6 +394,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hb.load()
+    if args.workload == "scaling":
+        rows = run_scaling(hb, torch, list(range(16, args.max_logN + 1)))
+        if rank == 0:
+            print(json.dumps({"workload": "exact-HBS black box, k=45, r=50, s=150, leaf 64",
+                              "unit": "ms", "rows": rows}), flush=True)
+        return
 
     def barrier():
         if world > 1:
