@@ -145,18 +145,18 @@ def dist_env():
 # ------------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the workload (cpu_baseline and --impl reference)
 
-def oracle_sample_time(N, r, s, leaf, rows=4096, sweep_N=8192):
+def oracle_sample_time(N, r, s, leaf, rows=4096, sweep_N=8192, workload="logkernel"):
     """Seconds the FP64 oracle would take for the full workload, from a bounded sample:
     Philox rows and sampling products for ``rows`` of the N rows, and the sweep of a
     ``sweep_N``-point problem of the same r, s, leaf, each scaled by its share of the work."""
     import numpy as np
-    from hbs_inputs import gaussian, log_kernel_rows
+    from hbs_inputs import double_layer_rows, gaussian, log_kernel_rows
     from oracle import philox
     from oracle.compress import compress
     from oracle.sample import sample_dense
 
     idx = np.arange(rows)
-    A_rows = log_kernel_rows(N, idx)                         # input, not timed
+    A_rows = (double_layer_rows if workload == "doublelayer" else log_kernel_rows)(N, idx)
     t0 = time.perf_counter()
     Om_rows = philox.gaussian_matrix(N, s, 0, SEED, rows=idx)
     Ps_rows = philox.gaussian_matrix(N, s, 1, SEED, rows=idx)
@@ -371,12 +371,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="logkernel", choices=["logkernel", "scaling"],
-                    help="logkernel: the timed N = 32768 log-kernel step (default); scaling: "
-                         "black-box exact-HBS compression for N = 2^16 .. 2^22")
+    ap.add_argument("--workload", default="logkernel",
+                    choices=["logkernel", "doublelayer", "scaling"],
+                    help="logkernel: the timed N = 32768 log-kernel step (default); doublelayer: "
+                         "the Section 5.1 boundary-integral operator with r = 30, m = 60, s = 90; "
+                         "scaling: black-box exact-HBS compression for N = 2^16 .. 2^22")
     ap.add_argument("--max-logN", type=int, default=22)
     args = ap.parse_args()
     N, r, s, leaf = args.N, R_DEF, S_DEF, LEAF_DEF
+    if args.workload == "doublelayer":
+        r, s, leaf = 30, 90, 60
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -387,7 +391,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2205_02990_gb300 as hb
-    from hbs_inputs import log_kernel_torch
+    from hbs_inputs import double_layer_torch, log_kernel_torch
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -415,7 +419,7 @@ def main():
 
     stream = torch.cuda.current_stream()
     modes = [args.only] if args.only else ["fp64", "mixed", "tc64"]
-    A = log_kernel_torch(N, "cuda")
+    A = (double_layer_torch if args.workload == "doublelayer" else log_kernel_torch)(N, "cuda")
     A32 = A.float() if any(MODES[m]["a"] == "f32" for m in modes) else None
     Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
     L = tree_nodes(N, leaf)
@@ -551,7 +555,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if head == "fp64" else "bf16x6/f32/f64", "data": "synthetic",
-        "config": {"workload": f"log-kernel N={N} r={r} s={s} leaf={leaf} dense",
+        "config": {"workload": ("double-layer BIE" if args.workload == "doublelayer" else "log-kernel")
+                               + f" N={N} r={r} s={s} leaf={leaf} dense",
                    "N": N, "r": r, "s": s, "leaf": leaf, "levels": L + 1, "mode": head,
                    "precision": MODES[head]["what"],
                    "l2": "inputs larger than L2 (A is %.1f GB, streamed every step)"
@@ -572,7 +577,7 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
-    if not args.only and not args.no_batched:
+    if not args.only and not args.no_batched and args.workload == "logkernel":
         for rr in results.values():
             rr["h"].free()
         results = {}
@@ -580,7 +585,7 @@ def main():
         torch.cuda.empty_cache()
         line["batched"] = run_batched(hb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_cpu, sample = oracle_sample_time(N, r, s, leaf)
+        t_cpu, sample = oracle_sample_time(N, r, s, leaf, workload=args.workload)
         line["cpu_baseline"] = {"value": N * s / t_cpu, "unit": UNIT, "cores": cpu_cores(),
                                 "kind": "oracle", "sample": sample}
     for rr in results.values():

@@ -16,6 +16,9 @@ stand in for them):
   and Gaussian leaf diagonal blocks. Its telescoping factors (Section 3.3) are returned too, with
   parent blocks D_tau = [[0, B_ab], [B_ba, 0]]; the dense matrix is assembled block by block from
   expanded bases, not through the apply algorithm.
+* ``double_layer``: the Nystrom (trapezoid) matrix of the boundary integral equation of Section
+  5.1, (1/2) I + K with the double-layer kernel on the same curve (a second operator of the kind
+  the paper compresses; the paper's own contour is only in a figure).
 * ``gaussian``: i.i.d. N(0, 1) arrays from numpy's PCG64 (used where test matrices are passed
   in as inputs rather than drawn by the method's own counter-based generator).
 
@@ -23,10 +26,12 @@ The tree used by ``exact_hbs`` is the one of Section 3.1 (ceil split, split whil
 larger than the leaf threshold); it is rebuilt here from that description.
 """
 
-from .generators import (CurvePoints, ExactHBS, curve_points, exact_hbs, exact_hbs_packed_torch,
+from .generators import (CurvePoints, ExactHBS, curve_points, double_layer, double_layer_rows,
+                         double_layer_torch, exact_hbs, exact_hbs_packed_torch,
                          gaussian, log_kernel, log_kernel_rows, log_kernel_torch, pack_telescoping,
                          packed_layout, seed_for)
 
-__all__ = ["CurvePoints", "ExactHBS", "curve_points", "exact_hbs", "exact_hbs_packed_torch",
+__all__ = ["CurvePoints", "ExactHBS", "curve_points", "double_layer", "double_layer_rows",
+           "double_layer_torch", "exact_hbs", "exact_hbs_packed_torch",
            "gaussian", "log_kernel", "log_kernel_rows", "log_kernel_torch", "pack_telescoping",
            "packed_layout", "seed_for"]

@@ -239,3 +239,66 @@ def exact_hbs_packed_torch(N, leaf_max, k, seed, device):
             D[:, k:, :k] = gauss(cnt, k, k)
             view[:, blk - n * n:] = D.reshape(cnt, n * n)
     return out
+
+
+def _curve_geometry(N):
+    """Points, outward unit normals, arc-length weights (trapezoid rule) and curvature of
+    r(theta) = 1 + 0.3 cos 5 theta at theta_i = 2 pi i / N (counter-clockwise)."""
+    th = 2.0 * np.pi * np.arange(N) / N
+    r = 1.0 + 0.3 * np.cos(5 * th)
+    dr = -1.5 * np.sin(5 * th)
+    d2r = -7.5 * np.cos(5 * th)
+    x, y = r * np.cos(th), r * np.sin(th)
+    dx, dy = dr * np.cos(th) - r * np.sin(th), dr * np.sin(th) + r * np.cos(th)
+    d2x = d2r * np.cos(th) - 2 * dr * np.sin(th) - r * np.cos(th)
+    d2y = d2r * np.sin(th) + 2 * dr * np.cos(th) - r * np.sin(th)
+    speed = np.hypot(dx, dy)
+    nx, ny = dy / speed, -dx / speed
+    kappa = (dx * d2y - dy * d2x) / speed ** 3
+    w = speed * 2.0 * np.pi / N
+    return x, y, nx, ny, w, kappa
+
+
+def double_layer_rows(N, rows, cols=None):
+    """Rows of the Nystrom matrix of the boundary integral equation of Section 5.1 on the same
+    curve: (1/2) delta_ij + w_j (x_i - y_j) . n(y_j) / (4 pi |x_i - y_j|^2) (constant as printed
+    in the paper), with the kernel's smooth diagonal limit -kappa_i / (8 pi) times w_i."""
+    x, y, nx, ny, w, kappa = _curve_geometry(N)
+    rows = np.asarray(rows)
+    cols = np.arange(N) if cols is None else np.asarray(cols)
+    ddx = x[rows][:, None] - x[cols][None, :]
+    ddy = y[rows][:, None] - y[cols][None, :]
+    num = ddx * nx[cols][None, :] + ddy * ny[cols][None, :]
+    den = ddx ** 2 + ddy ** 2
+    same = rows[:, None] == cols[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        K = num / (4.0 * np.pi * np.where(same, 1.0, den))
+    diag = -kappa / (8.0 * np.pi)
+    K = np.where(same, diag[rows][:, None], K) * w[cols][None, :]
+    return K + 0.5 * same
+
+
+def double_layer(N):
+    return double_layer_rows(N, np.arange(N))
+
+
+def double_layer_torch(N, device, dtype=None, row_block=4096):
+    """Dense double-layer Nystrom matrix built by torch on ``device`` in row blocks."""
+    import torch
+    dtype = dtype or torch.float64
+    x, y, nx, ny, w, kappa = (torch.as_tensor(v, device=device) for v in _curve_geometry(N))
+    A = torch.empty((N, N), dtype=dtype, device=device)
+    for r0 in range(0, N, row_block):
+        r1 = min(N, r0 + row_block)
+        ddx = x[r0:r1, None] - x[None, :]
+        ddy = y[r0:r1, None] - y[None, :]
+        den = ddx * ddx + ddy * ddy
+        idx = torch.arange(r0, r1, device=device)
+        den[idx - r0, idx] = 1.0
+        K = (ddx * nx[None, :] + ddy * ny[None, :]) / (4.0 * np.pi * den)
+        K[idx - r0, idx] = -kappa[idx] / (8.0 * np.pi)
+        K = K * w[None, :]
+        K[idx - r0, idx] += 0.5
+        A[r0:r1] = K.to(dtype)
+        del ddx, ddy, den, K
+    return A

@@ -270,3 +270,16 @@ def test_full_size_log_kernel_sampled_parity(hb):
     hb.hbs_apply(h, X, Out)
     assert rel(host(Out), host(A @ X)) <= 1e-5
     del A
+
+
+def test_double_layer_accuracy_matches_oracle(hb):
+    # the Section 5.1 boundary integral operator with the paper's r = 30, m = 60, s = 90
+    from hbs_inputs import double_layer
+    N, r, s, leaf = 2048, 30, 90, 60
+    A = double_layer(N)
+    h = pipeline(hb, A, N, r, s, leaf, 8)
+    At = gpu_dense(hb, h, N)
+    Ao = oapply.dense(ocompress(*osample(A, N, s, 8), r, leaf))
+    e_gpu, e_orc = rel(At, A), rel(Ao, A)
+    assert e_gpu <= 1e-6 and e_orc <= 1e-6
+    assert e_gpu <= 3 * e_orc and e_orc <= 3 * e_gpu
