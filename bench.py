@@ -219,6 +219,10 @@ MODES = {
                        "nullspace QR / pseudo-inverse and FP32 bases, D_tau and merges"),
     "tc64": dict(sample=2, sweep=0, a="f32",
                  what="A stored FP32; bf16x6 products on tcgen05 tensor cores; FP64 sweep"),
+    "oz64": dict(sample=3, sweep=3, a="f64",
+                 what="A stored FP64; FP64-class products from 7 exact 8-bit digits per entry "
+                      "(28 bf16 digit-pair products on tcgen05 tensor cores, exact FP32 sums); "
+                      "FP64 sweep"),
 }
 
 
@@ -418,7 +422,7 @@ def main():
         return float(t.item())
 
     stream = torch.cuda.current_stream()
-    modes = [args.only] if args.only else ["fp64", "mixed", "tc64"]
+    modes = [args.only] if args.only else ["fp64", "oz64", "mixed", "tc64"]
     A = (double_layer_torch if args.workload == "doublelayer" else log_kernel_torch)(N, "cuda")
     A32 = A.float() if any(MODES[m]["a"] == "f32" for m in modes) else None
     Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
@@ -534,7 +538,14 @@ def main():
 
     value = world * N * s * args.steps / res["elapsed"]
     flops_product = 2.0 * N * N * s                          # one of the two products
-    if MODES[head]["sample"] == 0:
+    if MODES[head]["sample"] == 3:
+        peak = BF16_TFLOPS_SUSTAINED
+        achieved = 28 * flops_product / res["per_launch"] / 1e12
+        roofline = {"kernel": "oz_gemm (28 exact bf16 digit-pair products per FP64 product)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+    elif MODES[head]["sample"] == 0:
         peak = SM_COUNT_GB300 * FP64_DFMA_PER_CLK_PER_SM * 2 * 2070e6 / 1e12
         achieved = flops_product / res["per_launch"] / 1e12
         roofline = {"kernel": "sample_gemm_f64 (Y = A Omega, Z = A^T Psi)", "bound": "alu",
@@ -554,7 +565,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if head == "fp64" else "bf16x6/f32/f64", "data": "synthetic",
+        "dtype": {"fp64": "f64", "oz64": "f64 (exact bf16 digit products)", "mixed": "bf16x6/f32/f64",
+                  "tc64": "bf16x6/f64"}[head], "data": "synthetic",
         "config": {"workload": ("double-layer BIE" if args.workload == "doublelayer" else "log-kernel")
                                + f" N={N} r={r} s={s} leaf={leaf} dense",
                    "N": N, "r": r, "s": s, "leaf": leaf, "levels": L + 1, "mode": head,
@@ -565,8 +577,8 @@ def main():
         "rel_error": {"opnorm_power20": res.get("rel_error"), "vs": "dense A"},
         "compress_ms": res["elapsed"] / args.steps * 1e3,
         "sweep_gflop": sweep_flops(N, r, s, leaf) / 1e9,
-        "gpu_launches": args.steps * ((2 + 2 + 2 * (L + 1)) if MODES[head]["sample"] == 0
-                                      else (2 + 6 + 2 * (L + 1))),
+        "gpu_launches": args.steps * ({0: 2 + 2 + 2, 2: 2 + 6, 3: 2 + 3 + 4}[MODES[head]["sample"]]
+                                      + 2 * (L + 1)),
         "roofline": roofline,
         "clocks": res["clocks"],
         "modes": {m: {"ms_per_step": rr["elapsed"] / args.steps * 1e3,

@@ -51,7 +51,15 @@ typedef enum {
   HBS_PREC_MIXED_BF16X3 = 1,/* sampling: FP32 A and FP64 Omega split into 2 bfloat16 slices,
                                3 slice products on the tensor cores, FP32 accumulation over
                                chunks of 2048, chunks summed in FP64 (~16 significant bits) */
-  HBS_PREC_MIXED_BF16X6 = 2 /* as above with 3 slices and 6 products (~24 significant bits) */
+  HBS_PREC_MIXED_BF16X6 = 2,/* as above with 3 slices and 6 products (~24 significant bits) */
+  HBS_PREC_FP64_TC = 3      /* sampling: FP64 A and Omega written as 7 exact 8-bit digits per
+                               entry (one exponent per 64-wide block; an error-free splitting in
+                               the manner of Ozaki et al., Numer. Algorithms 59, 2012), the 28
+                               digit-pair products with exactly representable FP32 sums on the
+                               tensor cores, double-float accumulation over 2048 indices, FP64
+                               beyond: FP64-class products (~55-bit terms). Sweep in FP64 as
+                               HBS_PREC_FP64. Needs N <= 2^20 and about 28 N^2 bytes of device
+                               scratch (the digit planes of A in both orientations) */
 } hbs_precision;
 
 typedef enum { HBS_F64 = 0, HBS_F32 = 1 } hbs_dtype;
@@ -92,7 +100,8 @@ typedef struct {
 
 /* Precision of the products (hbs_sample, hbs_sample_products): HBS_PREC_FP64 needs a dense A in
  * HBS_F64 or a callback; the mixed precisions need a dense A in HBS_F32 with lda a multiple of
- * 4 and s <= 256, and keep Omega, Psi, Y, Z in FP64. */
+ * 4 and s <= 256; HBS_PREC_FP64_TC needs a dense A in HBS_F64 (any lda >= N), s <= 256 and
+ * N <= 2^20. All keep Omega, Psi, Y, Z in FP64. */
 
 /* Randomized samples (Algorithm 2, first block): draws Omega (stream 0) and Psi (stream 1)
  * from `seed` as hbs_draw_gaussian does, then Y = A Omega and Z = A^* Psi.
@@ -109,8 +118,9 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
                         const double* Psi, double* Y, double* Z, void* cuda_stream);
 
 /* Waits for `cuda_stream` and returns the device status of the tensor-core sampling on the
- * current device since the last call: HBS_OK, or HBS_ERR_TIMEOUT if a bounded wait inside the
- * kernel gave up (the products are then invalid). Clears the status. */
+ * current device since the last call: HBS_OK, HBS_ERR_TIMEOUT if a bounded wait inside the
+ * kernel gave up, or HBS_ERR_NUMERIC if HBS_PREC_FP64_TC met an Inf or NaN (the products are
+ * then invalid). Clears the status. */
 int hbs_sample_sync(void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------------

@@ -232,7 +232,8 @@ void free_handle(hbs_handle* h) {
 
 // The sweep's launches, one side and one finish kernel per height, finest height first.
 cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
-  const bool fp32_finish = h->precision != HBS_PREC_FP64;
+  const bool fp32_finish =
+      h->precision == HBS_PREC_MIXED_BF16X3 || h->precision == HBS_PREC_MIXED_BF16X6;
   for (auto& H : h->heights) {
     cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
                                             H.max_s, fp32_finish, H.R, h->d_status, st);
@@ -303,13 +304,18 @@ static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, 
   if (!op || !a || !b || !c || !d || s < 1 || op->N < 1)
     return fail(HBS_ERR_ARG, "%s: bad arguments", who);
   if (precision != HBS_PREC_FP64 && precision != HBS_PREC_MIXED_BF16X3 &&
-      precision != HBS_PREC_MIXED_BF16X6)
+      precision != HBS_PREC_MIXED_BF16X6 && precision != HBS_PREC_FP64_TC)
     return fail(HBS_ERR_ARG, "%s: unknown precision %d", who, precision);
   if (!op->A && !op->fn) return fail(HBS_ERR_ARG, "%s: operator has neither A nor fn", who);
   if (op->A && op->lda < op->N) return fail(HBS_ERR_ARG, "%s: lda < N", who);
   if (precision == HBS_PREC_FP64) {
     if (op->A && op->dtype != HBS_F64)
       return fail(HBS_ERR_UNSUPPORTED, "%s: FP64 products need a FP64 dense A", who);
+  } else if (precision == HBS_PREC_FP64_TC) {
+    if (!op->A || op->dtype != HBS_F64)
+      return fail(HBS_ERR_UNSUPPORTED, "%s: digit products need a dense FP64 A", who);
+    if (s > 256 || op->N > (int64_t(1) << 20))
+      return fail(HBS_ERR_UNSUPPORTED, "%s: digit products need s <= 256 and N <= 2^20", who);
   } else {
     if (!op->A || op->dtype != HBS_F32)
       return fail(HBS_ERR_UNSUPPORTED, "%s: mixed products need a dense FP32 A", who);
@@ -324,6 +330,16 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
   const int rc = check_operator(op, s, precision, Omega, Psi, Y, Z, "hbs_sample_products");
   if (rc != HBS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (precision == HBS_PREC_FP64_TC) {
+    static const int digits = [] {                 // 7 (default) or 6 digits per entry
+      const char* v = getenv("HBS_OZ_DIGITS");
+      return (v && atoi(v) == 6) ? 6 : 7;
+    }();
+    cudaError_t e = hbs::launch_sample_dense_oz(static_cast<const double*>(op->A), op->lda, op->N,
+                                                Omega, Psi, s, Y, Z, digits, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core digit sampling");
+    return ok();
+  }
   if (precision != HBS_PREC_FP64) {
     static const int kchunk = [] {                 // tuning override; 0 = split for occupancy
       const char* v = getenv("HBS_TC_KCHUNK");
@@ -353,11 +369,14 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
 int hbs_sample_sync(void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
-  int status = 0;
+  int status = 0, oz_status = 0;
   e = hbs::sample_tc_status(&status, true);
+  if (e == cudaSuccess) e = hbs::sample_oz_status(&oz_status, true);
   if (e != cudaSuccess) return cuda_fail(e, "sampling status read");
-  if (status & hbs::kStatusTimeout)
+  if ((status | oz_status) & hbs::kStatusTimeout)
     return fail(HBS_ERR_TIMEOUT, "tensor-core sampling: a bounded device wait gave up");
+  if (oz_status & hbs::kStatusNumeric)
+    return fail(HBS_ERR_NUMERIC, "tensor-core digit sampling: A or a test matrix has an Inf or NaN");
   return ok();
 }
 
@@ -377,7 +396,7 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
   if (!out || !probs || batch < 1) return fail(HBS_ERR_ARG, "hbs_plan: bad arguments");
   *out = nullptr;
   if (precision != HBS_PREC_FP64 && precision != HBS_PREC_MIXED_BF16X3 &&
-      precision != HBS_PREC_MIXED_BF16X6)
+      precision != HBS_PREC_MIXED_BF16X6 && precision != HBS_PREC_FP64_TC)
     return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: unknown precision %d", precision);
   for (int i = 0; i < batch; ++i) {
     const int rc = check_problem(probs[i], i);

@@ -72,6 +72,16 @@ cudaError_t launch_sample_dense_tc(const float* A, int64_t lda, int64_t N, const
                                    const double* Ps, int s, double* Y, double* Z, int slices,
                                    int kchunk, cudaStream_t st);
 cudaError_t sample_tc_status(int* host_status, bool clear);
+// Column tiling shared by the tensor-core products: s <= 128 as one tile of s rounded up to 32,
+// wider s as tiles of 128 (sample_tc.cu).
+void column_tiles(int s, int* BN, int* BNt);
+// FP64-class sampling by exact bfloat16 digit products on the tensor cores (sample_oz.cu):
+// A FP64 row-major (any lda >= N), digits = 6 or 7, s <= 256, N <= 2^20. The scratch it grows
+// holds the device status word at its start.
+cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, const double* Om,
+                                   const double* Ps, int s, double* Y, double* Z, int digits,
+                                   cudaStream_t st);
+cudaError_t sample_oz_status(int* host_status, bool clear);
 cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st);
 
 }  // namespace hbs

@@ -87,26 +87,44 @@ __device__ void make_reflector(Real* M, int ld, int j, int cols, Real* tau, Real
   }
 }
 
-// In-place Householder LQ of M (rows x cols, rows <= cols, leading dimension ld).
+// In-place Householder LQ of M (rows x cols, rows <= cols, leading dimension ld), with a
+// one-step look-ahead: while warps 1.. apply reflector j to rows j+2.., warp 0 applies it to row
+// j+1 and at once generates reflector j+1, so the serial reflector generation (a norm, a square
+// root and two divisions on the FP64 pipe) is off the critical path of the other warps. Row j+1
+// is updated by a whole warp (a 32-lane reduction), the other rows by groups of G lanes.
 template <class Real>
 __device__ void lq_factor(Real* M, int ld, int rows, int cols, Real* tau, Real* rdiag,
                           int* status) {
-  const int gid = threadIdx.x / G, q = threadIdx.x % G;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int gid = (threadIdx.x - 32) / G, q = threadIdx.x % G;   // groups of warps 1..
+  constexpr int kGroups = (THREADS - 32) / G;
+  make_reflector(M, ld, 0, cols, tau, rdiag, status);
+  __syncthreads();
   for (int j = 0; j < rows; ++j) {
-    make_reflector(M, ld, j, cols, tau, rdiag, status);
-    __syncthreads();
     const Real tj = tau[j];
     const Real* v = M + static_cast<size_t>(j) * ld;
-    const int remaining = rows - j - 1;
-    for (int base = 0; base < remaining; base += NGROUPS) {
-      const int i = j + 1 + base + gid;
-      const bool active = i < rows;
-      Real* ri = M + static_cast<size_t>(active ? i : j) * ld;
-      Real part = 0;
-      for (int k = j + q; k < cols; k += G) part = fma(ri[k], v[k], part);
-      const Real w = group_sum(part) * tj;
-      if (active)
-        for (int k = j + q; k < cols; k += G) ri[k] = fma(-w, v[k], ri[k]);
+    if (warp == 0) {
+      if (j + 1 < rows) {                                         // row j+1, then reflector j+1
+        Real* ri = M + static_cast<size_t>(j + 1) * ld;
+        Real part = 0;
+        for (int k = j + lane; k < cols; k += 32) part = fma(ri[k], v[k], part);
+        const Real w = warp_sum(part) * tj;
+        for (int k = j + lane; k < cols; k += 32) ri[k] = fma(-w, v[k], ri[k]);
+        __syncwarp();
+        make_reflector(M, ld, j + 1, cols, tau, rdiag, status);
+      }
+    } else {
+      const int remaining = rows - j - 2;                       // rows j+2 .. rows-1
+      for (int base = 0; base < remaining; base += kGroups) {
+        const int i = j + 2 + base + gid;
+        const bool active = i < rows;
+        Real* ri = M + static_cast<size_t>(active ? i : j) * ld;
+        Real part = 0;
+        for (int k = j + q; k < cols; k += G) part = fma(ri[k], v[k], part);
+        const Real w = group_sum(part) * tj;
+        if (active)
+          for (int k = j + q; k < cols; k += G) ri[k] = fma(-w, v[k], ri[k]);
+      }
     }
     __syncthreads();
   }

@@ -27,6 +27,7 @@ HBS_ERR_UNSUPPORTED = -8
 HBS_PREC_FP64 = 0
 HBS_PREC_MIXED_BF16X3 = 1
 HBS_PREC_MIXED_BF16X6 = 2
+HBS_PREC_FP64_TC = 3
 HBS_F64 = 0
 HBS_F32 = 1
 
