@@ -20,9 +20,9 @@
 // order and under any rounding of its adder. Pairs with i + j <= S - 1 are formed, S(S+1)/2
 // bf16 tile products per window; each dropped pair weighs at most 2^(2-8S) of max|a| max|b|.
 //
-// Accumulation. The diagonal d of a window is one accumulator in tensor memory (two of them,
-// ping-pong): the MMA thread fills one while eight drain warps scale the other by its power of
-// two (exact) and add it to a double-float running sum kept in tensor memory (hi + lo: TwoSum in
+// Accumulation. The diagonal d of a window is one accumulator in tensor memory (four of them,
+// several): the MMA thread fills one while eight drain warps scale another by its power of
+// two (exact) and add it to a double-float running sum kept in registers (hi + lo: TwoSum in
 // FP32, then a Fast2Sum renormalisation that keeps |lo| <= ulp(hi) / 2, so that every addition
 // errs by at most ~2^-48 of the running sum). A CTA's reduction range is at most 32 windows (2048 indices); the ranges are summed
 // in FP64 by the reduce kernel. Within a range, scales are taken relative to the largest block
@@ -49,7 +49,8 @@
 namespace hbs {
 namespace {
 
-constexpr int kOzThreads = 320;
+constexpr int kDrainWarps = 8;                  // two per quarter of tensor-memory lanes
+constexpr int kOzThreads = 64 + 32 * kDrainWarps;
 constexpr int OBM = 128;                       // rows of C per CTA (MMA M)
 constexpr int OBK = 64;                        // window: reduction indices per digit tile
 constexpr int kDigitTileA = OBM * OBK * 2;     // one bf16 digit tile of A
@@ -75,9 +76,9 @@ __device__ __forceinline__ int block_exponent(uint64_t m, int* status) {
   return e - 1021;
 }
 
-// Balanced base-256 digits of round(x 2^(8S - E)) (|x| < 2^(E-1)), most significant first.
+// round(x 2^(8S - E)) for |x| < 2^(E-1): an integer of magnitude <= 2^(8S-1).
 template <int S>
-__device__ __forceinline__ void to_digits(double x, int E, int (&d)[S]) {
+__device__ __forceinline__ int64_t scaled_integer(double x, int E) {
   const uint64_t u = static_cast<uint64_t>(__double_as_longlong(x));
   const int ex = static_cast<int>((u >> 52) & 0x7ff);
   uint64_t m = u & ((1ull << 52) - 1);
@@ -87,99 +88,100 @@ __device__ __forceinline__ void to_digits(double x, int E, int (&d)[S]) {
     p = ex - 1075;
   }
   const int sh = p + 8 * S - E;
-  int64_t X = 0;
+  uint64_t X = 0;
   if (E != kNoExp && m != 0 && ex != 0x7ff) {
-    if (sh >= 0) X = static_cast<int64_t>(m << min(sh, 10));
-    else if (sh > -60) X = static_cast<int64_t>((m + (1ull << (-sh - 1))) >> (-sh));
+    if (sh >= 0) X = m << min(sh, 10);
+    else if (sh > -60) X = (m + (1ull << (-sh - 1))) >> (-sh);
   }
-  if (u >> 63) X = -X;
-#pragma unroll
-  for (int i = S - 1; i > 0; --i) {
-    const int di = static_cast<int>((X + 128) & 255) - 128;
-    d[i] = di;
-    X = (X - di) >> 8;
-  }
-  d[0] = static_cast<int>(X);
+  return (u >> 63) ? -static_cast<int64_t>(X) : static_cast<int64_t>(X);
 }
 
-// bfloat16 bits of an integer |v| <= 128 (exact: at most 8 significant bits).
-__device__ __forceinline__ uint32_t digit_bf16(int v) {
-  const float f = __int_as_float(0x4B000000 + v + 256) - 8388864.0f;   // 2^23 + 256
-  return __float_as_uint(f) >> 16;
+// The balanced base-256 digits of X (d_i in [-128, 127], the leading one in [-128, 128]) are
+// the bytes of V = X + 128 (256^(S-1) + ... + 1) less 128 each (the leading one: V's bits from
+// 8(S-1) up), with no carries to propagate. This returns the bfloat16 bits of digit i (0: most
+// significant) from the two 32-bit halves of V: the byte is placed under the exponent of 2^23
+// by a byte permute and 2^23 + 128 is subtracted in FP32, exactly.
+template <int S>
+__device__ __forceinline__ uint32_t digit_bits(uint32_t vl, uint32_t vh, int i) {
+  const int k = S - 1 - i;                              // byte position from the bottom
+  uint32_t w;
+  if (k == S - 1) w = 0x4B000000u | (vh >> (8 * (S - 1) - 32));
+  else if (k < 4) w = __byte_perm(vl, 0x4B000000u, 0x7650u | static_cast<uint32_t>(k));
+  else w = __byte_perm(vh, 0x4B000000u, 0x7650u | static_cast<uint32_t>(k - 4));
+  return __float_as_uint(__fsub_rn(__uint_as_float(w), 8388736.0f));   // 2^23 + 128
+}
+
+template <int S>
+__device__ __forceinline__ uint64_t digit_offset() {
+  uint64_t c = 0;
+#pragma unroll
+  for (int i = 0; i < S; ++i) c = (c << 8) | 128u;
+  return c;
 }
 
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
-// Writes 16 consecutive digits-of-x (one per plane) for a thread's 16 elements.
+// bfloat16 digits of one entry into S planes (plane_stride apart).
 template <int S>
-__device__ __forceinline__ void store_digits16(const double (&x)[16], int E, uint16_t* dst,
-                                               size_t plane_stride) {
-  uint32_t w[S][8];
+__device__ __forceinline__ void store_digits(double x, int E, uint16_t* dst, size_t plane_stride) {
+  const uint64_t v = static_cast<uint64_t>(scaled_integer<S>(x, E)) + digit_offset<S>();
+  const uint32_t vl = static_cast<uint32_t>(v), vh = static_cast<uint32_t>(v >> 32);
 #pragma unroll
-  for (int j = 0; j < 16; j += 2) {
-    int d0[S], d1[S];
-    to_digits<S>(x[j], E, d0);
-    to_digits<S>(x[j + 1], E, d1);
+  for (int i = 0; i < S; ++i) dst[i * plane_stride] = static_cast<uint16_t>(digit_bits<S>(vl, vh, i) >> 16);
+}
+
+__device__ __forceinline__ uint64_t warp_max64(uint64_t m) {
 #pragma unroll
-    for (int i = 0; i < S; ++i) w[i][j / 2] = digit_bf16(d0[i]) | (digit_bf16(d1[i]) << 16);
-  }
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    uint4* q = reinterpret_cast<uint4*>(dst + i * plane_stride);
-    q[0] = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
-    q[1] = make_uint4(w[i][4], w[i][5], w[i][6], w[i][7]);
-  }
+  for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_xor_sync(0xffffffffu, m, o));
+  return m;
 }
 
 // One 64 x 64 block of A: exponents per row (EY) and per column (EZ), digit planes of A (Yd,
 // row-major) and of A^* (Zd). Planes: S x N rows of ldd entries; ldd a multiple of 64.
+// Warp w handles rows (then columns) 8w .. 8w+7; lane l the entries l and l + 32 along them, so
+// that both the row and the column reads of the tile (pitch 65) are free of bank conflicts and
+// every digit store of a warp covers 64 contiguous bytes.
 template <int S>
 __global__ void __launch_bounds__(256)
     oz_split_a(const double* __restrict__ A, int64_t lda, int64_t N, uint16_t* __restrict__ Yd,
                uint16_t* __restrict__ Zd, int64_t ldd, int16_t* __restrict__ EY,
                int16_t* __restrict__ EZ, int W, int* status) {
   __shared__ double tile[64][65];
-  __shared__ int rowE[64], colE[64];
   const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 64, c0 = static_cast<int64_t>(blockIdx.x) * 64;
-  const int t = threadIdx.x;
-  for (int e = t; e < 64 * 64; e += 256) {
-    const int r = e >> 6, c = e & 63;
-    const int64_t gr = r0 + r, gc = c0 + c;
-    tile[r][c] = (gr < N && gc < N) ? A[gr * lda + gc] : 0.0;
-  }
-  __syncthreads();
-  const int g = t >> 2, part = t & 3;                 // row / column g, quarter `part`
-  uint64_t mr = 0, mc = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    mr = umax64(mr, abs_bits(tile[g][part * 16 + j]));
-    mc = umax64(mc, abs_bits(tile[part * 16 + j][g]));
-  }
-  mr = umax64(mr, __shfl_xor_sync(0xffffffffu, mr, 1));
-  mr = umax64(mr, __shfl_xor_sync(0xffffffffu, mr, 2));
-  mc = umax64(mc, __shfl_xor_sync(0xffffffffu, mc, 1));
-  mc = umax64(mc, __shfl_xor_sync(0xffffffffu, mc, 2));
-  if (part == 0) {
-    rowE[g] = block_exponent(mr, status);
-    colE[g] = block_exponent(mc, status);
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = warp * 8 + rr;
+    const int64_t gr = r0 + r;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gc = c0 + lane + 32 * h;
+      tile[r][lane + 32 * h] = (gr < N && gc < N) ? A[gr * lda + gc] : 0.0;
+    }
   }
   __syncthreads();
-  if (t < 64) {
-    if (r0 + t < N) EY[(r0 + t) * W + blockIdx.x] = static_cast<int16_t>(rowE[t]);
-  } else if (t < 128) {
-    if (c0 + t - 64 < N) EZ[(c0 + t - 64) * W + blockIdx.y] = static_cast<int16_t>(colE[t - 64]);
-  }
   const size_t plane = static_cast<size_t>(N) * ldd;
-  double x[16];
-  if (r0 + g < N) {                                   // row g of A: digits for Y = A Omega
-#pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = tile[g][part * 16 + j];
-    store_digits16<S>(x, rowE[g], Yd + (r0 + g) * ldd + c0 + part * 16, plane);
+#pragma unroll 1
+  for (int rr = 0; rr < 8; ++rr) {                    // rows of A: digits for Y = A Omega
+    const int r = warp * 8 + rr;
+    const double x0 = tile[r][lane], x1 = tile[r][lane + 32];
+    const int E = block_exponent(warp_max64(umax64(abs_bits(x0), abs_bits(x1))), status);
+    if (r0 + r >= N) continue;
+    if (lane == 0) EY[(r0 + r) * W + blockIdx.x] = static_cast<int16_t>(E);
+    uint16_t* dst = Yd + (r0 + r) * ldd + c0 + lane;
+    store_digits<S>(x0, E, dst, plane);
+    store_digits<S>(x1, E, dst + 32, plane);
   }
-  if (c0 + g < N) {                                   // column g of A: digits for Z = A^* Psi
-#pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = tile[part * 16 + j][g];
-    store_digits16<S>(x, colE[g], Zd + (c0 + g) * ldd + r0 + part * 16, plane);
+#pragma unroll 1
+  for (int cc = 0; cc < 8; ++cc) {                    // columns of A: digits for Z = A^* Psi
+    const int c = warp * 8 + cc;
+    const double x0 = tile[lane][c], x1 = tile[lane + 32][c];
+    const int E = block_exponent(warp_max64(umax64(abs_bits(x0), abs_bits(x1))), status);
+    if (c0 + c >= N) continue;
+    if (lane == 0) EZ[(c0 + c) * W + blockIdx.y] = static_cast<int16_t>(E);
+    uint16_t* dst = Zd + (c0 + c) * ldd + r0 + lane;
+    store_digits<S>(x0, E, dst, plane);
+    store_digits<S>(x1, E, dst + 32, plane);
   }
 }
 
@@ -215,11 +217,11 @@ __global__ void __launch_bounds__(256)
     const int c = e >> 6, kk = e & 63;
     const int64_t k = k0 + kk;
     const double x = (c < s && k < N) ? X[k * s + c] : 0.0;
-    int d[S];
-    to_digits<S>(x, E, d);
+    const uint64_t v = static_cast<uint64_t>(scaled_integer<S>(x, E)) + digit_offset<S>();
 #pragma unroll
     for (int i = 0; i < S; ++i)
-      out[i * plane + static_cast<size_t>(c) * ldd + k] = static_cast<uint16_t>(digit_bf16(d[i]));
+      out[i * plane + static_cast<size_t>(c) * ldd + k] = static_cast<uint16_t>(
+          digit_bits<S>(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32), i) >> 16);
   }
 }
 
@@ -233,14 +235,80 @@ struct OzArgs {
   const int16_t* EA;   // [M][W] exponent of row m of op(A) over window w
   const int16_t* EB;   // [W] exponent of the test matrix over window w
   float2* partial;     // [splits][M][BNt] (hi, lo), in units of 2^rexp
-  int* rexp;           // [splits][M] reference exponent of each split's row sums
+  int* rexp;           // [splits][M] reference exponent of each split's row sums (kEmptyRange: 0)
   int* status;
 };
+
+constexpr int kAccBufs = 4;          // accumulators in tensor memory, 128 columns each
+constexpr int kExactDiags = 4;       // diagonals added by TwoSum; the later ones weigh < 2^-30 of
+                                     // d = 0 and go into lo with one FMA (error < 2^-48 of hi)
+constexpr int kEmptyRange = -(1 << 20);
 
 __device__ __forceinline__ float pow2f(int e) {
   return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : 0.0f;
 }
 
+// (hi, lo) += v: TwoSum, then a Fast2Sum renormalisation that keeps |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+  const float t = __fadd_rn(lo, err);
+  const float h2 = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(h2, s));
+  hi = h2;
+}
+
+template <bool ACC>
+__device__ __forceinline__ void mma_bf16_c(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "n"(ACC ? 1 : 0)
+      : "memory");
+}
+
+// The MMAs of diagonal D: pairs (i, D - i), four K = 16 steps each; on the last diagonal in
+// groups (k, S-1-k), (S-1-k, k), each group committed to freed[k] so that the producer can refill
+// those digits while the rest of the window runs. Fully unrolled with the descriptors of the
+// digit tiles precomputed, so that the single issuing thread spends few instructions per MMA.
+template <int S, int D>
+__device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad)[S],
+                                               const uint64_t (&bd)[S], uint32_t idesc,
+                                               uint64_t* freed) {
+  if constexpr (D < S - 1) {
+#pragma unroll
+    for (int i = 0; i <= D; ++i)
+#pragma unroll
+      for (int kk = 0; kk < OBK / 16; ++kk) {
+        if (i == 0 && kk == 0) mma_bf16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+        else mma_bf16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+      }
+  } else {
+    constexpr int G = (S + 1) / 2;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int i = t == 0 ? k : S - 1 - k;
+        if (t == 1 && i == k) continue;
+#pragma unroll
+        for (int kk = 0; kk < OBK / 16; ++kk) {
+          if (k == 0 && t == 0 && kk == 0) mma_bf16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+          else mma_bf16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+        }
+      }
+      mma_commit(&freed[k]);
+    }
+  }
+}
+
+// Drain warps: warp w covers TMEM lanes 32 (w % 4) .. + 31 (rows of the tile) and the 16-column
+// chunks c = part + P cc of the BN columns (part = (w - 2) / 4, P = drain warps / 4); its running
+// sums stay in registers. The drain shares each scheduler with the producer or the MMA thread,
+// whose issue slots must not be crowded out, so it stays at two warps per scheduler.
 template <int S>
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -252,11 +320,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int tile_b = BN * 128;
   uint8_t* opA = smem;                                   // S digit tiles of A
   uint8_t* opB = opA + S * kDigitTileA;                  // S digit tiles of the test matrix
+  constexpr int G = (S + 1) / 2;                         // digit groups {k, S-1-k}
   uint64_t* full = reinterpret_cast<uint64_t*>(opB + S * tile_b);   // S: digit i landed
-  uint64_t* empty = full + S;                            // the window's MMAs are done
-  uint64_t* acc_full = empty + 1;                        // 2
-  uint64_t* acc_empty = acc_full + 2;                    // 2
-  uint64_t* mma_done = acc_empty + 2;
+  uint64_t* freed = full + S;                            // G: group k's last MMAs are done
+  uint64_t* acc_full = freed + G;                        // kAccBufs
+  uint64_t* acc_empty = acc_full + kAccBufs;             // kAccBufs
+  uint64_t* mma_done = acc_empty + kAccBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -264,15 +333,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int n0 = blockIdx.z * BN;
   const int w_begin = blockIdx.y * a.wchunk;
   const int nw = max(0, min(a.W, w_begin + a.wchunk) - w_begin);
-  constexpr uint32_t kTmemCols = 512;                    // acc0, acc1, hi, lo
-  constexpr uint32_t kHi = 256, kLo = 384;
+  constexpr uint32_t kTmemCols = 128 * kAccBufs;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
-    mbar_init(empty, 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int k = 0; k < G; ++k) mbar_init(&freed[k], 1);
+    for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 8);
+      mbar_init(&acc_empty[i], kDrainWarps);
     }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -292,53 +360,76 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (warp == 0) {
     if (lane == 0) {                                     // ---- TMA producer ----
       bool ok = true;
-      int issued = 0;                                    // windows whose loads were issued
+      int wfull = 0, kpart = 0;                          // windows issued; groups of the next
       for (int w = 0; w < nw && ok; ++w) {
-        if (w > 0) ok = mbar_wait(empty, (w - 1) & 1, a.status);
-        if (!ok) break;
         const int k0 = (w_begin + w) * OBK;
-#pragma unroll
-        for (int i = 0; i < S; ++i) {
-          mbar_expect_tx(&full[i], kDigitTileA + tile_b);
-          tma_load_2d(opA + i * kDigitTileA, &tmA, &full[i], k0, i * a.M + m0);
-          tma_load_2d(opB + i * tile_b, &tmB, &full[i], k0, i * a.BNt + n0);
+        // digit groups in the order the previous window frees them: {0, S-1}, {1, S-2}, ...
+        // -- the low digits, which this window's first diagonals need, land first
+        for (int k = 0; k < G && ok; ++k) {
+          if (w > 0) ok = mbar_wait(&freed[k], (w - 1) & 1, a.status);
+          if (!ok) break;
+          for (int i = k; ; i = S - 1 - k) {
+            mbar_expect_tx(&full[i], kDigitTileA + tile_b);
+            tma_load_2d(opA + i * kDigitTileA, &tmA, &full[i], k0, i * a.M + m0);
+            tma_load_2d(opB + i * tile_b, &tmB, &full[i], k0, i * a.BNt + n0);
+            if (i == S - 1 - k) break;
+          }
+          kpart = k + 1;
         }
-        issued = w + 1;
+        if (!ok) break;
+        wfull = w + 1;
+        kpart = 0;
+        if (w + 1 < nw) {                                // next window into L2 meanwhile
+#pragma unroll
+          for (int i = 0; i < S; ++i) {
+            tma_prefetch_2d(&tmA, k0 + OBK, i * a.M + m0);
+            tma_prefetch_2d(&tmB, k0 + OBK, i * a.BNt + n0);
+          }
+        }
       }
-      if (issued > 0)                                    // copies must land before exit
-        for (int i = 0; i < S; ++i) mbar_wait(&full[i], (issued - 1) & 1, a.status, false);
+      for (int i = 0; i < S; ++i) {                      // copies must land before exit (the
+        const int grp = i < S - 1 - i ? i : S - 1 - i;   // earlier ones were consumed)
+        const int issued = wfull + (grp < kpart ? 1 : 0);
+        if (issued > 0) mbar_wait(&full[i], (issued - 1) & 1, a.status, false);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {                                     // ---- MMA issuer ----
       const uint32_t idesc = idesc_bf16(OBM, BN);
-      const uint32_t abase = su32(opA), bbase = su32(opB);
+      uint64_t ad[S], bd[S];
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        ad[i] = sw128_desc(su32(opA) + i * kDigitTileA);
+        bd[i] = sw128_desc(su32(opB) + i * tile_b);
+      }
       bool ok = true;
       int g = 0;                                         // diagonals issued
       for (int w = 0; w < nw && ok; ++w) {
         for (int d = 0; d < S && ok; ++d, ++g) {
-          const int b = g & 1;
-          if (g >= 2) ok = mbar_wait(&acc_empty[b], ((g >> 1) - 1) & 1, a.status);
+          const int b = g % kAccBufs;
+          if (g >= kAccBufs) ok = mbar_wait(&acc_empty[b], ((g / kAccBufs) - 1) & 1, a.status);
           if (ok) ok = mbar_wait(&full[d], w & 1, a.status);
           if (!ok) break;
           tc_fence_after();
           const uint32_t acc = tmem + static_cast<uint32_t>(b * 128);
-          for (int i = 0; i <= d; ++i) {
-            const uint64_t ad = sw128_desc(abase + i * kDigitTileA);
-            const uint64_t bd = sw128_desc(bbase + (d - i) * tile_b);
-#pragma unroll
-            for (int kk = 0; kk < OBK / 16; ++kk)
-              mma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc, (i == 0 && kk == 0) ? 0u : 1u);
+          switch (d) {
+            case 0: issue_diagonal<S, 0>(acc, ad, bd, idesc, freed); break;
+            case 1: issue_diagonal<S, 1>(acc, ad, bd, idesc, freed); break;
+            case 2: issue_diagonal<S, 2>(acc, ad, bd, idesc, freed); break;
+            case 3: issue_diagonal<S, 3>(acc, ad, bd, idesc, freed); break;
+            case 4: issue_diagonal<S, 4>(acc, ad, bd, idesc, freed); break;
+            case 5: issue_diagonal<S, 5>(acc, ad, bd, idesc, freed); break;
+            default: issue_diagonal<S, S - 1>(acc, ad, bd, idesc, freed); break;
           }
           mma_commit(&acc_full[b]);
         }
-        if (ok) mma_commit(empty);
       }
       mma_commit(mma_done);                              // all issued MMAs finished
       mbar_wait(mma_done, 0, a.status, false);
     }
-  } else {                                               // ---- drain (warps 2..9) ----
-    const int quarter = warp & 3;                        // TMEM lanes 32*quarter .. +31
-    const int half = (warp - 2) >> 2;                    // 32-column chunks c with c % 2 == half
+  } else {                                               // ---- drain warps ----
+    const int quarter = warp & 3;
+    const int part = (warp - 2) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     const int row = m0 + quarter * 32 + lane;
     int RA = kNoExp, RB = kNoExp;                        // largest exponents over the range
@@ -346,75 +437,67 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       if (row < a.M) RA = max(RA, static_cast<int>(a.EA[static_cast<size_t>(row) * a.W + w]));
       RB = max(RB, static_cast<int>(a.EB[w]));
     }
-    const int nchunks = BN / 32;
+    constexpr int P = kDrainWarps / 4;                   // drain warps per lane quarter
+    constexpr int CPT = 8 / P;                           // 16-column chunks per thread
+    const int nchunks = BN / 16;
+    float hi[CPT][16], lo[CPT][16];
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) hi[cc][j] = lo[cc][j] = 0.0f;
     bool ok = true;
     int g = 0;
+    const size_t erow = static_cast<size_t>(row < a.M ? row : 0) * a.W;
+    int ea_next = (row < a.M && nw > 0) ? a.EA[erow + w_begin] : kNoExp;
     for (int w = 0; w < nw && ok; ++w) {
       const int wabs = w_begin + w;
-      const int ea = row < a.M ? a.EA[static_cast<size_t>(row) * a.W + wabs] : kNoExp;
+      const int ea = ea_next;                            // loaded a window ahead
+      if (w + 1 < nw && row < a.M) ea_next = a.EA[erow + wabs + 1];
       const int eb = a.EB[wabs];
       const bool zero = (ea == kNoExp || eb == kNoExp);
       const int base = (ea - RA) + (eb - RB) - 16;
       for (int d = 0; d < S && ok; ++d, ++g) {
-        const int b = g & 1;
-        ok = mbar_wait(&acc_full[b], (g >> 1) & 1, a.status);
+        const int b = g % kAccBufs;
+        ok = mbar_wait(&acc_full[b], (g / kAccBufs) & 1, a.status);
         if (!ok) break;
         tc_fence_after();
         const float scale = zero ? 0.0f : pow2f(base - 8 * d);
-        for (int c = half; c < nchunks; c += 2) {
-          uint32_t x[32], hi[32], lo[32];
-          tmem_ld32(tmem + lane_base + static_cast<uint32_t>(b * 128 + 32 * c), x);
-          if (g == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              hi[j] = __float_as_uint(__fmul_rn(__uint_as_float(x[j]), scale));
-              lo[j] = 0u;
-            }
-          } else {
-            tmem_ld32(tmem + lane_base + kHi + static_cast<uint32_t>(32 * c), hi);
-            tmem_ld32(tmem + lane_base + kLo + static_cast<uint32_t>(32 * c), lo);
+        for (int cc = 0; cc < CPT; ++cc) {
+          const int c = part + P * cc;
+          if (c >= nchunks) continue;
+          uint32_t x[16];
+          tmem_ld16(tmem + lane_base + static_cast<uint32_t>(b * 128 + 16 * c), x);
+          if (d < kExactDiags) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {   // (hi, lo) += x * scale: TwoSum, then renormalise
-              const float h = __uint_as_float(hi[j]);
-              const float v = __fmul_rn(__uint_as_float(x[j]), scale);
-              const float s = __fadd_rn(h, v);
-              const float bp = __fsub_rn(s, h);
-              const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-              const float t = __fadd_rn(__uint_as_float(lo[j]), err);
-              const float h2 = __fadd_rn(s, t);
-              hi[j] = __float_as_uint(h2);
-              lo[j] = __float_as_uint(__fsub_rn(t, __fsub_rn(h2, s)));
-            }
+            for (int j = 0; j < 16; ++j)
+              df_add(hi[cc][j], lo[cc][j], __fmul_rn(__uint_as_float(x[j]), scale));
+          } else {                                        // below 2^-30 of the running sum
+#pragma unroll
+            for (int j = 0; j < 16; ++j) lo[cc][j] = __fmaf_rn(__uint_as_float(x[j]), scale, lo[cc][j]);
           }
-          tmem_st32(tmem + lane_base + kHi + static_cast<uint32_t>(32 * c), hi);
-          tmem_st32(tmem + lane_base + kLo + static_cast<uint32_t>(32 * c), lo);
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[b]);
       }
     }
-    tc_fence_after();
-    float2* out = a.partial + (static_cast<size_t>(blockIdx.y) * a.M + row) * a.BNt + n0;
-    if (half == 0 && row < a.M)
-      a.rexp[static_cast<size_t>(blockIdx.y) * a.M + row] =
-          (RA == kNoExp || RB == kNoExp) ? 0 : RA + RB;
-    if (ok && g == nw * S && nw > 0) {
-      for (int c = half; c < nchunks; c += 2) {
-        uint32_t hi[32], lo[32];
-        tmem_ld32(tmem + lane_base + kHi + static_cast<uint32_t>(32 * c), hi);
-        tmem_ld32(tmem + lane_base + kLo + static_cast<uint32_t>(32 * c), lo);
-        if (row < a.M) {
+    if (row < a.M) {
+      if (part == 0)
+        a.rexp[static_cast<size_t>(blockIdx.y) * a.M + row] =
+            (RA == kNoExp || RB == kNoExp) ? kEmptyRange : RA + RB;
+      if (ok && g == nw * S) {
+        float2* out = a.partial + (static_cast<size_t>(blockIdx.y) * a.M + row) * a.BNt + n0;
 #pragma unroll
-          for (int j = 0; j < 32; j += 2)
-            *reinterpret_cast<float4*>(out + 32 * c + j) =
-                make_float4(__uint_as_float(hi[j]), __uint_as_float(lo[j]),
-                            __uint_as_float(hi[j + 1]), __uint_as_float(lo[j + 1]));
+        for (int cc = 0; cc < CPT; ++cc) {
+          const int c = part + P * cc;
+          if (c >= nchunks) continue;
+#pragma unroll
+          for (int j = 0; j < 16; j += 2)
+            *reinterpret_cast<float4*>(out + 16 * c + j) =
+                make_float4(hi[cc][j], lo[cc][j], hi[cc][j + 1], lo[cc][j + 1]);
         }
       }
-    } else if (nw == 0 && row < a.M) {
-      for (int c = half; c < nchunks; c += 2)
-        for (int j = 0; j < 32; ++j) out[32 * c + j] = make_float2(0.f, 0.f);
     }
   }
   tc_fence_before();
@@ -426,7 +509,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   }
 }
 
-// C[i][c] = sum over splits of 2^rexp (hi + lo), in FP64, in split order.
+// C[i][c] = sum over splits of 2^rexp (hi + lo): the splits' double-floats are brought to the
+// row's largest split exponent R (exact powers of two), added as double-floats in split order,
+// and the result is scaled by 2^R in FP64.
 __global__ void oz_reduce(const float2* __restrict__ partial, const int* __restrict__ rexp,
                           int splits, int64_t M, int BNt, int s, double* __restrict__ C) {
   const int64_t total = M * s;
@@ -434,12 +519,21 @@ __global__ void oz_reduce(const float2* __restrict__ partial, const int* __restr
        idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = idx / s;
     const int c = static_cast<int>(idx % s);
-    double acc = 0.0;
-    for (int sp = 0; sp < splits; ++sp) {
-      const float2 p = partial[(sp * M + i) * BNt + c];
-      acc += scalbn(static_cast<double>(p.x) + static_cast<double>(p.y), rexp[sp * M + i]);
+    int R = kEmptyRange;
+    for (int sp = 0; sp < splits; ++sp) R = max(R, rexp[sp * M + i]);
+    float H = 0.0f, Lo = 0.0f;
+    if (R != kEmptyRange) {
+      for (int sp = 0; sp < splits; ++sp) {
+        const int e = rexp[sp * M + i];
+        if (e == kEmptyRange) continue;
+        const float scale = pow2f(e - R);
+        const float2 p = partial[(sp * M + i) * BNt + c];
+        df_add(H, Lo, __fmul_rn(p.x, scale));
+        Lo = __fadd_rn(Lo, __fmul_rn(p.y, scale));
+      }
     }
-    C[idx] = acc;
+    C[idx] = R == kEmptyRange ? 0.0
+                              : scalbn(static_cast<double>(H) + static_cast<double>(Lo), R);
   }
 }
 
@@ -480,7 +574,7 @@ cudaError_t oz_scratch(size_t bytes, void** out) {
 size_t align1k(size_t b) { return (b + 1023) / 1024 * 1024; }
 
 size_t oz_smem_bytes(int S, int BN) {
-  return static_cast<size_t>(S) * (kDigitTileA + BN * 128) + 256 + 1024;
+  return static_cast<size_t>(S) * (kDigitTileA + BN * 128) + 256 + 1024;   // tiles, barriers, align
 }
 
 template <int S>
@@ -533,9 +627,9 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
   CUtensorMap mAy, mAz, mBo, mBp;
   const uint64_t row_bytes = static_cast<uint64_t>(ldd) * 2;
   if (!make_map(&mAy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Yd, N, S * N, row_bytes, OBK, OBM,
-                CU_TENSOR_MAP_SWIZZLE_128B) ||
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B) ||
       !make_map(&mAz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Zd, N, S * N, row_bytes, OBK, OBM,
-                CU_TENSOR_MAP_SWIZZLE_128B) ||
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B) ||
       !make_map(&mBo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bo, N, S * BNt, row_bytes, OBK, BN,
                 CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&mBp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bp, N, S * BNt, row_bytes, OBK, BN,

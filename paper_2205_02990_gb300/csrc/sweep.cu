@@ -22,7 +22,9 @@
 // Finish kernel (FP64, or FP32 in the mixed precisions): one CTA per node. col(., r) is an
 // unpivoted Householder QR whose first r columns are formed explicitly, then D_tau and the
 // parent's blocks. Since UU^* U = U, the product U^* D needed by the merge equals U^* T2^*
-// with T2 = (I - VV^*) Z Psi^+ and is taken from there; D V is formed from D.
+// with T2 = (I - VV^*) Z Psi^+ and is taken from there; D V is formed from D. In FP64 the
+// merges into the parent's blocks run in a third kernel with several CTAs per node (column
+// chunks); the FP32 finish does them itself.
 //
 // Reflectors use LAPACK's sign choice (beta = -sign(alpha) ||x||; identity when the tail is
 // zero) and are stored with their leading 1 explicit. Mapping: 256 threads = 32 groups of 8
@@ -339,25 +341,66 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   __syncthreads();
 
-  // ---- this node's rows of the parent's blocks (Eq. omega_tau_and_y_tau) ----
-  for (int e = threadIdx.x; e < r * s; e += THREADS) {
-    const int c = e / s, k = e % s;
-    Real om = 0, ps = 0, y = 0, z = 0;
+  // ---- U^* D = G1 and (D V)^* = Hs (r x n each) for the merge kernel, in the spent XY, XZ ----
+  for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    const int c = e / n, i = e % n;
+    tk.XY[e] = static_cast<double>(G1[c * ldX + i]);
+    tk.XZ[e] = static_cast<double>(Hs[e]);
+  }
+}
+
+// ---- merge kernel: this node's rows of the parent's blocks (Eq. omega_tau_and_y_tau) ------------
+// Grid (node, chunk of kMergeCols columns, pass). Pass 0: V^* Omega_tau and
+// U^* Y_tau - (U^* D) Omega_tau; pass 1: U^* Psi_tau and V^* Z_tau - (D V)^* Psi_tau, with U^* D
+// and (D V)^* as the FP64 finish kernel left them in XY and XZ (r x n). Splitting the merges
+// (the larger part of a node's finish flops) over many CTAs keeps the upper levels, which have
+// few nodes, from waiting on one SM's FP64 pipe.
+constexpr int kMergeCols = 32;
+
+__global__ void __launch_bounds__(THREADS)
+    node_merge(const NodeTask* __restrict__ tasks) {
+  extern __shared__ double msm[];
+  const NodeTask tk = tasks[blockIdx.x];
+  if (tk.is_root) return;
+  const int n = tk.n, r = tk.r, s = tk.s;
+  const int k0 = blockIdx.y * kMergeCols;
+  if (k0 >= s) return;
+  const int kw = min(kMergeCols, s - k0);
+  const int pass = blockIdx.z;
+  const double* T = pass ? tk.Ps : tk.Om;
+  const double* S = pass ? tk.Z : tk.Y;
+  const double* Bt = pass ? tk.U : tk.V;               // reduces the test block
+  const double* Bs = pass ? tk.V : tk.U;               // reduces the sample block
+  const double* H = pass ? tk.XZ : tk.XY;              // (D V)^* or U^* D, r x n
+  double* outT = pass ? tk.Ps_p : tk.Om_p;
+  double* outS = pass ? tk.Z_p : tk.Y_p;
+  double* Ts = msm;                                    // n x kw
+  double* Ss = Ts + static_cast<size_t>(n) * kw;       // n x kw
+  double* Bts = Ss + static_cast<size_t>(n) * kw;      // n x r
+  double* Bss = Bts + static_cast<size_t>(n) * r;      // n x r
+  double* Hsm = Bss + static_cast<size_t>(n) * r;      // r x n
+  for (int e = threadIdx.x; e < n * kw; e += THREADS) {
+    const int i = e / kw, k = e % kw;
+    Ts[e] = T[static_cast<size_t>(i) * s + k0 + k];
+    Ss[e] = S[static_cast<size_t>(i) * s + k0 + k];
+  }
+  for (int e = threadIdx.x; e < n * r; e += THREADS) {
+    Bts[e] = Bt[e];
+    Bss[e] = Bs[e];
+    Hsm[e] = H[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * kw; e += THREADS) {
+    const int c = e / kw, k = e % kw;
+    double t = 0.0, y = 0.0;
     for (int i = 0; i < n; ++i) {
-      const size_t ik = static_cast<size_t>(i) * s + k;
-      const Real u = static_cast<Real>(U[i * r + c]), v = static_cast<Real>(V[i * r + c]);
-      const Real omk = static_cast<Real>(tk.Om[ik]), psk = static_cast<Real>(tk.Ps[ik]);
-      om = fma(v, omk, om);
-      ps = fma(u, psk, ps);
-      y = fma(u, static_cast<Real>(tk.Y[ik]), y);
-      y = fma(-G1[c * ldX + i], omk, y);
-      z = fma(v, static_cast<Real>(tk.Z[ik]), z);
-      z = fma(-Hs[c * n + i], psk, z);
+      const double tv = Ts[i * kw + k];
+      t = fma(Bts[i * r + c], tv, t);
+      y = fma(Bss[i * r + c], Ss[i * kw + k], y);
+      y = fma(-Hsm[c * n + i], tv, y);
     }
-    tk.Om_p[e] = static_cast<double>(om);
-    tk.Ps_p[e] = static_cast<double>(ps);
-    tk.Y_p[e] = static_cast<double>(y);
-    tk.Z_p[e] = static_cast<double>(z);
+    outT[c * s + k0 + k] = t;
+    outS[c * s + k0 + k] = y;
   }
 }
 
@@ -504,6 +547,10 @@ size_t finish_smem_reals(int n, int r) {
          static_cast<size_t>(r) * n + r;
 }
 
+size_t merge_smem_doubles(int n, int r) {
+  return 2 * static_cast<size_t>(n) * kMergeCols + 3 * static_cast<size_t>(n) * r;
+}
+
 // FP32 finish: the FP64 finish's regions plus the staged U, V, WY, WZ (floats).
 size_t finish_f32_smem_floats(int n, int r) {
   return finish_smem_reals(n, r) + 2 * static_cast<size_t>(n) * r + 2 * static_cast<size_t>(n) * n;
@@ -546,7 +593,9 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
   const size_t fin_bytes = fp32_finish ? finish_f32_smem_floats(max_n, max_r) * sizeof(float)
                                        : finish_smem_reals(max_n, max_r) * sizeof(double);
-  if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
+  if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes ||
+      merge_smem_doubles(max_n, max_r) * sizeof(double) > kMaxNodeSmemBytes)
+    return cudaErrorInvalidValue;
   const int splits = row_splits > 0 ? std::max(1, std::min(row_splits, std::max(1, max_n)))
                                     : side_row_splits(ntasks, max_n);
   const dim3 side_grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
@@ -578,6 +627,14 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
     if (max_n <= 8 * G) finish(node_finish<double, 8>);
     else if (max_n <= 16 * G) finish(node_finish<double, 16>);
     else finish(node_finish<double, 24>);
+    if (e != cudaSuccess) return e;
+    e = allow_smem(node_merge);
+    if (e != cudaSuccess) return e;
+    const dim3 merge_grid(static_cast<unsigned>(ntasks),
+                          static_cast<unsigned>((max_s + kMergeCols - 1) / kMergeCols), 2u);
+    node_merge<<<merge_grid, THREADS, merge_smem_doubles(max_n, max_r) * sizeof(double), st>>>(
+        d_tasks);
+    e = cudaGetLastError();
   }
   return e;
 }
