@@ -38,7 +38,8 @@ N_DEF, R_DEF, S_DEF, LEAF_DEF, SEED = 32768, 40, 120, 64, 220502990 + 200
 SM_COUNT_GB300 = 152
 FP64_DFMA_PER_CLK_PER_SM = 2          # GB300: FP64 at 1/64 of the FP32 rate (1.25 TF nominal)
 FP64_PROBE_TFLOPS = 1.056             # measured DFMA throughput on this GB300 (see profiles/)
-GEMM_TRAFFIC_8192 = 550.9e6           # dram read+write of one sample_gemm_f64 launch, N = 8192
+GEMM_READ_8192 = 549.46e6             # dram bytes read by one sample_gemm_f64 launch, N = 8192
+GEMM_WRITE_8192 = 42.30e6             # dram bytes written (split-K partials) by that launch
 BF16_TFLOPS_SUSTAINED = 1666.9        # measured dense bf16 peak on this machine's GB300 (sustained)
 
 
@@ -541,7 +542,8 @@ def main():
     if MODES[head]["sample"] == 3:
         peak = BF16_TFLOPS_SUSTAINED
         achieved = 28 * flops_product / res["per_launch"] / 1e12
-        roofline = {"kernel": "oz_gemm (28 exact bf16 digit-pair products per FP64 product)",
+        roofline = {"kernel": "digit products per FP64 product (oz_split_a/b + oz_gemm + oz_reduce; "
+                              "28 exact bf16 digit-pair products)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
                     "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
@@ -550,8 +552,9 @@ def main():
         achieved = flops_product / res["per_launch"] / 1e12
         roofline = {"kernel": "sample_gemm_f64 (Y = A Omega, Z = A^T Psi)", "bound": "alu",
                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": GEMM_TRAFFIC_8192 * (N / 8192) ** 2,
-                    "traffic_source": "ncu capture at N=8192 scaled by (N/8192)^2",
+                    "traffic": GEMM_READ_8192 * (N / 8192) ** 2 + GEMM_WRITE_8192 * (N / 8192),
+                    "traffic_source": "ncu capture at N=8192: reads (A) scaled by (N/8192)^2, "
+                                      "writes (split partials) by N/8192",
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
                     "probe_peak": FP64_PROBE_TFLOPS}
     else:
