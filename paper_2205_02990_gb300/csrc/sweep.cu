@@ -265,139 +265,142 @@ __global__ void __launch_bounds__(THREADS, 2)
                   side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
 }
 
-// ---- finish kernel: bases, D_tau and the parent's blocks, in Real precision ----------------
+// ---- FP64 finish: bases, D_tau and the parent's blocks in three kernels --------------------
+//
+// With P = U^* WY, Q = U^* WZ^* (r x n) and R = Q V (r x r), Eq. (d_tau_formula) reads
+//   D = (I - UU^*) WY + UU^* ((I - VV^*) WZ)^* = WY + U (Q - P - R V^*),
+// so every column block of D needs only its own columns of P and Q plus the small R. The
+// merges (Eq. omega_tau_and_y_tau) are U^* (Y - D Omega) and V^* (Z - D^* Psi) and need D only.
+// node_bases (node, side) -> U, V; node_dblk_a (node, column block) -> P, Q; node_dblk_b
+// (node, column block) -> R, D; node_merge (node, column chunk, pass) -> the parent's blocks.
+// Upper levels, which have few nodes, thus spread each node over several SMs.
 
-template <class Real, int NS>
-__global__ void __launch_bounds__(THREADS, 1)
-    node_finish(const NodeTask* __restrict__ tasks, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_bytes[];
-  Real* smem = reinterpret_cast<Real*>(smem_bytes);
+// U = col(Y P, r) (side 0) or V = col(Z Q, r) (side 1): unpivoted Householder QR, first r
+// columns formed explicitly.
+template <int NS>
+__global__ void __launch_bounds__(THREADS)
+    node_bases(const NodeTask* __restrict__ tasks, int* status) {
+  extern __shared__ double bsm[];
   const NodeTask tk = tasks[blockIdx.x];
   if (tk.is_root) return;
-  const int n = tk.n, r = tk.r, s = tk.s;
-  const int ldX = n + 1, ldT = n + 1;
-  Real* XT = smem;                                     // r x ldX: sample block of col, later G1
-  Real* T2 = XT + static_cast<size_t>(r) * ldX;        // n x ldT: (I - VV^*) WZ, later D
-  Real* Hs = T2 + static_cast<size_t>(n) * ldT;        // r x n: U^*(T2^* - WY), later (D V)^*
-  Real* tau2 = Hs + static_cast<size_t>(r) * n;        // r
-
-  // ---- U = col(Y P, r), V = col(Z Q, r) ----
-  for (int side = 0; side < 2; ++side) {
-    const double* X = side ? tk.XZ : tk.XY;
-    for (int e = threadIdx.x; e < n * r; e += THREADS)
-      XT[(e % r) * ldX + e / r] = static_cast<Real>(X[e]);
-    __syncthreads();
-    lq_factor<Real>(XT, ldX, r, n, tau2, nullptr, status);
-    form_basis<Real, NS>(XT, ldX, tau2, r, n, side ? tk.V : tk.U, r);
-    __syncthreads();
-  }
-
-  // ---- D_tau (Eq. d_tau_formula); U, V, WY, WZ were written before this point ----
-  const double* U = tk.U;
-  const double* V = tk.V;
-  const double* WY = tk.WY;
-  const double* WZ = tk.WZ;
-  Real* G1 = XT;
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, j = e % n;
-    Real acc = 0;
-    for (int i = 0; i < n; ++i)
-      acc = fma(static_cast<Real>(V[i * r + c]), static_cast<Real>(WZ[static_cast<size_t>(i) * n + j]), acc);
-    G1[c * ldX + j] = acc;
-  }
+  const int n = tk.n, r = tk.r;
+  const int ldX = n + 1;
+  double* XT = bsm;                                    // r x ldX: (Y P)^* or (Z Q)^*
+  double* tau2 = XT + static_cast<size_t>(r) * ldX;    // r
+  const double* X = blockIdx.y ? tk.XZ : tk.XY;
+  for (int e = threadIdx.x; e < n * r; e += THREADS) XT[(e % r) * ldX + e / r] = X[e];
   __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += THREADS) {
-    const int i = e / n, j = e % n;
-    Real acc = static_cast<Real>(WZ[e]);
-    for (int c = 0; c < r; ++c) acc = fma(-static_cast<Real>(V[i * r + c]), G1[c * ldX + j], acc);
-    T2[i * ldT + j] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, j = e % n;
-    Real h2 = 0, ky = 0;
+  lq_factor<double>(XT, ldX, r, n, tau2, nullptr, status);
+  form_basis<double, NS>(XT, ldX, tau2, r, n, blockIdx.y ? tk.V : tk.U, r);
+}
+
+// Columns [j0, j0 + nb) of P = U^* WY and Q = U^* WZ^*, into the spent XZ and XY (r x n).
+__global__ void __launch_bounds__(THREADS)
+    node_dblk_a(const NodeTask* __restrict__ tasks, int nb) {
+  const NodeTask tk = tasks[blockIdx.x];
+  if (tk.is_root) return;
+  const int n = tk.n, r = tk.r;
+  const int j0 = blockIdx.y * nb;
+  const int w = min(nb, n - j0);
+  if (w <= 0) return;
+  for (int e = threadIdx.x; e < r * w; e += THREADS) {
+    const int c = e / w, j = j0 + e % w;
+    double p = 0.0, q = 0.0;
     for (int i = 0; i < n; ++i) {
-      const Real u = static_cast<Real>(U[i * r + c]);
-      h2 = fma(u, T2[j * ldT + i], h2);
-      ky = fma(u, static_cast<Real>(WY[static_cast<size_t>(i) * n + j]), ky);
+      const double u = tk.U[i * r + c];
+      p = fma(u, tk.WY[static_cast<size_t>(i) * n + j], p);
+      q = fma(u, tk.WZ[static_cast<size_t>(j) * n + i], q);
     }
-    G1[c * ldX + j] = h2;
-    Hs[c * n + j] = h2 - ky;
+    tk.XZ[c * n + j] = p;
+    tk.XY[c * n + j] = q;
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += THREADS) {
-    const int i = e / n, j = e % n;
-    Real acc = static_cast<Real>(WY[e]);
-    for (int c = 0; c < r; ++c) acc = fma(static_cast<Real>(U[i * r + c]), Hs[c * n + j], acc);
-    tk.D[e] = static_cast<double>(acc);
-    T2[i * ldT + j] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, i = e % n;
-    Real acc = 0;
-    for (int j = 0; j < n; ++j) acc = fma(T2[i * ldT + j], static_cast<Real>(V[j * r + c]), acc);
-    Hs[c * n + i] = acc;
-  }
-  __syncthreads();
+}
 
-  // ---- U^* D = G1 and (D V)^* = Hs (r x n each) for the merge kernel, in the spent XY, XZ ----
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, i = e % n;
-    tk.XY[e] = static_cast<double>(G1[c * ldX + i]);
-    tk.XZ[e] = static_cast<double>(Hs[e]);
+// R = Q V (every column block forms it: r^2 n flops), then columns [j0, j0 + nb) of
+// M = Q - P - R V^* and of D = WY + U M.
+__global__ void __launch_bounds__(THREADS)
+    node_dblk_b(const NodeTask* __restrict__ tasks, int nb) {
+  extern __shared__ double dsm[];
+  const NodeTask tk = tasks[blockIdx.x];
+  if (tk.is_root) return;
+  const int n = tk.n, r = tk.r;
+  const int j0 = blockIdx.y * nb;
+  const int w = min(nb, n - j0);
+  if (w <= 0) return;
+  const double* Q = tk.XY;                             // r x n
+  const double* P = tk.XZ;                             // r x n
+  double* R = dsm;                                     // r x r
+  double* M = R + static_cast<size_t>(r) * r;          // r x w
+  for (int e = threadIdx.x; e < r * r; e += THREADS) {
+    const int c = e / r, f = e % r;
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) acc = fma(Q[c * n + j], tk.V[j * r + f], acc);
+    R[e] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < r * w; e += THREADS) {
+    const int c = e / w, j = j0 + e % w;
+    double acc = Q[c * n + j] - P[c * n + j];
+    for (int f = 0; f < r; ++f) acc = fma(-R[c * r + f], tk.V[j * r + f], acc);
+    M[c * w + (j - j0)] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * w; e += THREADS) {
+    const int i = e / w, jj = e % w;
+    double acc = tk.WY[static_cast<size_t>(i) * n + j0 + jj];
+    for (int c = 0; c < r; ++c) acc = fma(tk.U[i * r + c], M[c * w + jj], acc);
+    tk.D[static_cast<size_t>(i) * n + j0 + jj] = acc;
   }
 }
 
 // ---- merge kernel: this node's rows of the parent's blocks (Eq. omega_tau_and_y_tau) ------------
-// Grid (node, chunk of kMergeCols columns, pass). Pass 0: V^* Omega_tau and
-// U^* Y_tau - (U^* D) Omega_tau; pass 1: U^* Psi_tau and V^* Z_tau - (D V)^* Psi_tau, with U^* D
-// and (D V)^* as the FP64 finish kernel left them in XY and XZ (r x n). Splitting the merges
-// (the larger part of a node's finish flops) over many CTAs keeps the upper levels, which have
-// few nodes, from waiting on one SM's FP64 pipe.
-constexpr int kMergeCols = 32;
+// Grid (node, chunk of kw columns, pass). Pass 0: V^* Omega_tau and U^* (Y_tau - D Omega_tau);
+// pass 1: U^* Psi_tau and V^* (Z_tau - D^* Psi_tau). The chunk of the test and sample blocks is
+// staged in shared memory; D, U and V are read through L1 (each value is the same for the lanes
+// of a warp). Levels with few nodes take narrow chunks, so that they still spread over the SMs.
+constexpr int kMergeCols = 32;                          // widest chunk
 
 __global__ void __launch_bounds__(THREADS)
-    node_merge(const NodeTask* __restrict__ tasks) {
+    node_merge(const NodeTask* __restrict__ tasks, int chunk) {
   extern __shared__ double msm[];
   const NodeTask tk = tasks[blockIdx.x];
   if (tk.is_root) return;
   const int n = tk.n, r = tk.r, s = tk.s;
-  const int k0 = blockIdx.y * kMergeCols;
+  const int k0 = blockIdx.y * chunk;
   if (k0 >= s) return;
-  const int kw = min(kMergeCols, s - k0);
+  const int kw = min(chunk, s - k0);
   const int pass = blockIdx.z;
   const double* T = pass ? tk.Ps : tk.Om;
   const double* S = pass ? tk.Z : tk.Y;
   const double* Bt = pass ? tk.U : tk.V;               // reduces the test block
   const double* Bs = pass ? tk.V : tk.U;               // reduces the sample block
-  const double* H = pass ? tk.XZ : tk.XY;              // (D V)^* or U^* D, r x n
   double* outT = pass ? tk.Ps_p : tk.Om_p;
   double* outS = pass ? tk.Z_p : tk.Y_p;
   double* Ts = msm;                                    // n x kw
   double* Ss = Ts + static_cast<size_t>(n) * kw;       // n x kw
-  double* Bts = Ss + static_cast<size_t>(n) * kw;      // n x r
-  double* Bss = Bts + static_cast<size_t>(n) * r;      // n x r
-  double* Hsm = Bss + static_cast<size_t>(n) * r;      // r x n
   for (int e = threadIdx.x; e < n * kw; e += THREADS) {
     const int i = e / kw, k = e % kw;
     Ts[e] = T[static_cast<size_t>(i) * s + k0 + k];
     Ss[e] = S[static_cast<size_t>(i) * s + k0 + k];
   }
-  for (int e = threadIdx.x; e < n * r; e += THREADS) {
-    Bts[e] = Bt[e];
-    Bss[e] = Bs[e];
-    Hsm[e] = H[e];
+  __syncthreads();
+  // S <- S - op(D) T, each thread on its own entries (D for pass 0, D^* for pass 1)
+  for (int e = threadIdx.x; e < n * kw; e += THREADS) {
+    const int i = e / kw, k = e % kw;
+    double acc = Ss[e];
+    if (pass == 0)
+      for (int j = 0; j < n; ++j) acc = fma(-tk.D[static_cast<size_t>(i) * n + j], Ts[j * kw + k], acc);
+    else
+      for (int j = 0; j < n; ++j) acc = fma(-tk.D[static_cast<size_t>(j) * n + i], Ts[j * kw + k], acc);
+    Ss[e] = acc;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < r * kw; e += THREADS) {
     const int c = e / kw, k = e % kw;
     double t = 0.0, y = 0.0;
     for (int i = 0; i < n; ++i) {
-      const double tv = Ts[i * kw + k];
-      t = fma(Bts[i * r + c], tv, t);
-      y = fma(Bss[i * r + c], Ss[i * kw + k], y);
-      y = fma(-Hsm[c * n + i], tv, y);
+      t = fma(Bt[i * r + c], Ts[i * kw + k], t);
+      y = fma(Bs[i * r + c], Ss[i * kw + k], y);
     }
     outT[c * s + k0 + k] = t;
     outS[c * s + k0 + k] = y;
@@ -547,9 +550,15 @@ size_t finish_smem_reals(int n, int r) {
          static_cast<size_t>(r) * n + r;
 }
 
-size_t merge_smem_doubles(int n, int r) {
-  return 2 * static_cast<size_t>(n) * kMergeCols + 3 * static_cast<size_t>(n) * r;
+size_t merge_smem_doubles(int n) { return 2 * static_cast<size_t>(n) * kMergeCols; }
+size_t bases_smem_doubles(int n, int r) { return static_cast<size_t>(r) * (n + 1) + r; }
+size_t dblk_smem_doubles(int r, int nb) {
+  return static_cast<size_t>(r) * r + static_cast<size_t>(r) * nb;
 }
+
+// Column blocks per node for the D kernels: several where a level has few nodes (each block
+// re-forms the r x r product R, r^2 n flops, against ~4 r n^2 / blocks of its own work).
+int dblk_blocks(int ntasks) { return std::max(1, std::min(8, (2 * 152) / std::max(1, ntasks))); }
 
 // FP32 finish: the FP64 finish's regions plus the staged U, V, WY, WZ (floats).
 size_t finish_f32_smem_floats(int n, int r) {
@@ -592,9 +601,13 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   if (max_s > kMaxS) return cudaErrorInvalidValue;
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
   const size_t fin_bytes = fp32_finish ? finish_f32_smem_floats(max_n, max_r) * sizeof(float)
-                                       : finish_smem_reals(max_n, max_r) * sizeof(double);
+                                       : bases_smem_doubles(max_n, max_r) * sizeof(double);
+  const int blocks = dblk_blocks(ntasks);
+  const int nb = (max_n + blocks - 1) / blocks;
+  const size_t dblk_bytes = dblk_smem_doubles(max_r, nb) * sizeof(double);
+  const size_t merge_bytes = merge_smem_doubles(max_n) * sizeof(double);
   if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes ||
-      merge_smem_doubles(max_n, max_r) * sizeof(double) > kMaxNodeSmemBytes)
+      dblk_bytes > kMaxNodeSmemBytes || merge_bytes > kMaxNodeSmemBytes)
     return cudaErrorInvalidValue;
   const int splits = row_splits > 0 ? std::max(1, std::min(row_splits, std::max(1, max_n)))
                                     : side_row_splits(ntasks, max_n);
@@ -624,16 +637,35 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
     else if (max_n <= 16 * G) finish(node_finish_f32<16>);
     else finish(node_finish_f32<24>);
   } else {
-    if (max_n <= 8 * G) finish(node_finish<double, 8>);
-    else if (max_n <= 16 * G) finish(node_finish<double, 16>);
-    else finish(node_finish<double, 24>);
+    const dim3 bgrid(static_cast<unsigned>(ntasks), 2u);
+    auto bases = [&](auto kernel) {
+      e = allow_smem(kernel);
+      if (e == cudaSuccess) {
+        kernel<<<bgrid, THREADS, fin_bytes, st>>>(d_tasks, d_status);
+        e = cudaGetLastError();
+      }
+    };
+    if (max_n <= 8 * G) bases(node_bases<8>);
+    else if (max_n <= 16 * G) bases(node_bases<16>);
+    else bases(node_bases<24>);
+    if (e != cudaSuccess) return e;
+    const dim3 dgrid(static_cast<unsigned>(ntasks), static_cast<unsigned>(blocks));
+    node_dblk_a<<<dgrid, THREADS, 0, st>>>(d_tasks, nb);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = allow_smem(node_dblk_b);
+    if (e != cudaSuccess) return e;
+    node_dblk_b<<<dgrid, THREADS, dblk_bytes, st>>>(d_tasks, nb);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = allow_smem(node_merge);
     if (e != cudaSuccess) return e;
+    // about four CTAs per SM in all; chunks of 8 .. 32 columns
+    const int want = (4 * 152) / (2 * ntasks);
+    const int chunk = std::max(8, std::min(kMergeCols, (max_s + std::max(1, want) - 1) / std::max(1, want)));
     const dim3 merge_grid(static_cast<unsigned>(ntasks),
-                          static_cast<unsigned>((max_s + kMergeCols - 1) / kMergeCols), 2u);
-    node_merge<<<merge_grid, THREADS, merge_smem_doubles(max_n, max_r) * sizeof(double), st>>>(
-        d_tasks);
+                          static_cast<unsigned>((max_s + chunk - 1) / chunk), 2u);
+    node_merge<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
     e = cudaGetLastError();
   }
   return e;
