@@ -81,7 +81,12 @@ int hbs_draw_gaussian(int64_t N, int32_t s, uint32_t stream_id, uint64_t seed, d
 /* ---------------------------------------------------------------------------------------
  * The black-box operator (Section 1): either a dense matrix or a callback.
  * Dense: A != NULL, row-major N x N with leading dimension lda >= N, element type `dtype`
- *   (only HBS_F64 in this build), device memory.
+ *   (HBS_F64, or HBS_F32 for the mixed precisions), in device memory, or -- HBS_F64 with
+ *   HBS_PREC_FP64 only -- in page-locked host memory (cudaHostAlloc / cudaHostRegister): the
+ *   products then stream A through the device in row blocks on an internal stream, each
+ *   block's copy overlapping the previous block's products; the call stays ordered on
+ *   cuda_stream and A must stay valid until the stream has passed it. Pageable host memory
+ *   gives HBS_ERR_ARG.
  * Callback: A == NULL and fn != NULL. fn(user, trans, N, ncols, X, Out, cuda_stream) must
  *   queue Out = A X (trans = 0) or Out = A^* X (trans = 1) on cuda_stream, X and Out row-major
  *   N x ncols FP64 device arrays, and return 0 (any other value gives HBS_ERR_CALLBACK).

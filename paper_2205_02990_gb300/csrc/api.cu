@@ -299,6 +299,26 @@ int hbs_draw_gaussian(int64_t N, int32_t s, uint32_t stream_id, uint64_t seed, d
   return ok();
 }
 
+// A in page-locked (pinned or registered) host memory; anything else is taken as device memory.
+static bool host_resident(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+// Pageable host memory (not registered with CUDA) cannot be read by the kernels or streamed.
+static bool pageable_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeUnregistered;
+}
+
 static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, const void* a,
                           const void* b, const void* c, const void* d, const char* who) {
   if (!op || !a || !b || !c || !d || s < 1 || op->N < 1)
@@ -308,6 +328,10 @@ static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, 
     return fail(HBS_ERR_ARG, "%s: unknown precision %d", who, precision);
   if (!op->A && !op->fn) return fail(HBS_ERR_ARG, "%s: operator has neither A nor fn", who);
   if (op->A && op->lda < op->N) return fail(HBS_ERR_ARG, "%s: lda < N", who);
+  if (op->A && pageable_host(op->A))
+    return fail(HBS_ERR_ARG, "%s: A is pageable host memory (pin it or pass device memory)", who);
+  if (op->A && precision != HBS_PREC_FP64 && host_resident(op->A))
+    return fail(HBS_ERR_UNSUPPORTED, "%s: host-resident A is streamed in FP64 only", who);
   if (precision == HBS_PREC_FP64) {
     if (op->A && op->dtype != HBS_F64)
       return fail(HBS_ERR_UNSUPPORTED, "%s: FP64 products need a FP64 dense A", who);
@@ -354,9 +378,12 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
     return ok();
   }
   if (op->A) {
-    cudaError_t e = hbs::launch_sample_dense_f64(static_cast<const double*>(op->A), op->lda,
-                                                 op->N, Omega, Psi, s, Y, Z, st);
-    if (e != cudaSuccess) return cuda_fail(e, "sampling kernel");
+    const bool host = host_resident(op->A);
+    cudaError_t e = host ? hbs::launch_sample_host_f64(static_cast<const double*>(op->A), op->lda,
+                                                       op->N, Omega, Psi, s, Y, Z, st)
+                         : hbs::launch_sample_dense_f64(static_cast<const double*>(op->A), op->lda,
+                                                        op->N, Omega, Psi, s, Y, Z, st);
+    if (e != cudaSuccess) return cuda_fail(e, host ? "host-streamed sampling" : "sampling kernel");
     return ok();
   }
   if (op->fn(op->user, 0, op->N, s, Omega, Y, cuda_stream) != 0)

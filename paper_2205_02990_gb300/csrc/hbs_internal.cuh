@@ -65,6 +65,11 @@ cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, do
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,
                                     const double* Ps, int s, double* Y, double* Z,
                                     cudaStream_t st);
+// The same products for A in page-locked host memory, streamed through the device in row
+// blocks (a second stream copies block b+1 while block b is multiplied).
+cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, const double* Om,
+                                   const double* Ps, int s, double* Y, double* Z,
+                                   cudaStream_t st);
 // Tensor-core sampling (sample_tc.cu): A FP32 row-major (lda % 4 == 0), slices = 2 (bf16x3) or
 // 3 (bf16x6), s <= 256; kchunk = reduction columns per split (0: chosen to fill the GPU). The
 // scratch it grows holds the device status word at its start.

@@ -1,13 +1,18 @@
 // Dense FP64 sampling Y = A Omega, Z = A^* Psi (Algorithm 2, first block) on the FP64 pipe.
 //
-// C (N x s) = op(A) B with op(A) = A (Y) or A^T (Z); A row-major N x N (leading dimension
-// lda), B and C row-major N x s. One CTA computes a 64 x 128 tile of C (s <= 128 needs one
-// column tile) over one slice of the reduction; the K loop walks BK = 16 columns (Y) or rows
-// (Z) of A through shared memory, so that both products read A in coalesced 128-byte rows.
-// Each thread accumulates a 4 x 8 register tile. FP64 FMA is the bound: 2 N^2 s FMAs per
-// product. The reduction is cut into as many slices as make the CTA count a whole number of
-// waves (two CTAs per SM), so that no SM idles in a last partial wave; the slices' FP64
-// partials are summed in a fixed order, keeping the result deterministic.
+// C (M x s) = op(A) B with op(A) = A (Y; A stored M x K) or A^T (Z; A stored K x M); A
+// row-major with leading dimension lda, B (K x s) and C row-major. One CTA computes a 64 x 128
+// tile of C (s <= 128 needs one column tile) over one slice of the reduction; the K loop walks
+// BK = 16 columns (Y) or rows (Z) of A through shared memory, so that both products read A in
+// coalesced 128-byte rows. Each thread accumulates a 4 x 8 register tile. FP64 FMA is the
+// bound: 2 M K s FMAs per product. The reduction is cut into as many slices as make the CTA
+// count a whole number of waves (two CTAs per SM), so that no SM idles in a last partial wave;
+// the slices' FP64 partials are summed in a fixed order, keeping the result deterministic.
+//
+// A in page-locked host memory is streamed through the device in row blocks on a second
+// stream, each block's copy overlapping the products of the previous one: block b gives the
+// rows b of Y and one reduction slice of Z = sum_b A_b^* Psi_b; Z's slices are summed in block
+// order at the end.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -25,7 +30,7 @@ constexpr int ASTRIDE = BM + 1;   // padded so that the transposing stores of op
 
 template <bool TRANS>
 __global__ void __launch_bounds__(THREADS)
-    sample_gemm_f64(const double* __restrict__ A, int64_t lda, int64_t N,
+    sample_gemm_f64(const double* __restrict__ A, int64_t lda, int64_t M, int64_t K,
                     const double* __restrict__ B, int s, double* __restrict__ C, int64_t kslice,
                     int64_t ldc_split) {
   __shared__ double As[BK][ASTRIDE];   // As[k][m] = op(A)[m0 + m][k0 + k]
@@ -35,7 +40,7 @@ __global__ void __launch_bounds__(THREADS)
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
   const int c0 = blockIdx.y * BN;
   const int64_t kbeg = static_cast<int64_t>(blockIdx.z) * kslice;
-  const int64_t kend = min(N, kbeg + kslice);
+  const int64_t kend = min(K, kbeg + kslice);
   C += static_cast<int64_t>(blockIdx.z) * ldc_split;        // this slice's partial (or C itself)
 
   double acc[4][8];
@@ -52,11 +57,11 @@ __global__ void __launch_bounds__(THREADS)
       if (!TRANS) {            // A[m0 + m][k0 + k]: 16 consecutive threads read one row
         const int k = idx % BK, m = idx / BK;
         const int64_t gm = m0 + m, gk = k0 + k;
-        As[k][m] = (gm < N && gk < kend) ? A[gm * lda + gk] : 0.0;
+        As[k][m] = (gm < M && gk < kend) ? A[gm * lda + gk] : 0.0;
       } else {                 // A[k0 + k][m0 + m]: 64 consecutive threads read one row
         const int m = idx % BM, k = idx / BM;
         const int64_t gm = m0 + m, gk = k0 + k;
-        As[k][m] = (gm < N && gk < kend) ? A[gk * lda + gm] : 0.0;
+        As[k][m] = (gm < M && gk < kend) ? A[gk * lda + gm] : 0.0;
       }
     }
     // B tile: BK x BN = 2048 doubles, 8 per thread
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t gm = m0 + ty * 4 + i;
-    if (gm >= N) continue;
+    if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int gc = c0 + tx + 16 * j;
@@ -134,9 +139,9 @@ cudaError_t partial_buffer(size_t doubles, double** out) {
 
 // Reduction slices that make tiles x slices a whole number of waves of 2 x SM CTAs (about 16
 // waves; a slice keeps at least 64 reduction steps).
-int reduction_slices(int64_t N, int64_t tiles, int sms) {
+int reduction_slices(int64_t K, int64_t tiles, int sms) {
   const int64_t slots = 2 * static_cast<int64_t>(sms);
-  const int64_t max_slices = std::max<int64_t>(1, N / (64 * BK));
+  const int64_t max_slices = std::max<int64_t>(1, K / (64 * BK));
   int best = 1;
   double best_eff = 0.0;
   for (int64_t z = 1; z <= std::min<int64_t>(max_slices, 64); ++z) {
@@ -154,43 +159,155 @@ int reduction_slices(int64_t N, int64_t tiles, int sms) {
   return best;
 }
 
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 152;
+}
+
+// Slices of the reduction and their length (a multiple of BK) for an M x K product.
+void plan_slices(int64_t M, int64_t K, int s, int* nslices, int64_t* kslice) {
+  const int64_t tiles = ((M + BM - 1) / BM) * ((s + BN - 1) / BN);
+  const int slices = reduction_slices(K, tiles, sm_count());
+  *kslice = ((K + slices - 1) / slices + BK - 1) / BK * BK;
+  *nslices = static_cast<int>((K + *kslice - 1) / *kslice);
+}
+
+// Launches C (+ z * ldc) = the slices of op(A) B; C is M x s, slice z starts at C + z * ldc.
+cudaError_t launch_slices(bool trans, const double* A, int64_t lda, int64_t M, int64_t K,
+                          const double* B, int s, double* C, int nslices, int64_t kslice,
+                          int64_t ldc, cudaStream_t st) {
+  const dim3 grid(static_cast<unsigned>((M + BM - 1) / BM), static_cast<unsigned>((s + BN - 1) / BN),
+                  static_cast<unsigned>(nslices));
+  if (trans) sample_gemm_f64<true><<<grid, THREADS, 0, st>>>(A, lda, M, K, B, s, C, kslice, ldc);
+  else sample_gemm_f64<false><<<grid, THREADS, 0, st>>>(A, lda, M, K, B, s, C, kslice, ldc);
+  return cudaGetLastError();
+}
+
+// C = op(A) B, through the partial buffer when the reduction is split.
+cudaError_t product(bool trans, const double* A, int64_t lda, int64_t M, int64_t K,
+                    const double* B, int s, double* C, cudaStream_t st) {
+  int nslices;
+  int64_t kslice;
+  plan_slices(M, K, s, &nslices, &kslice);
+  const int64_t count = M * s;
+  if (nslices == 1) return launch_slices(trans, A, lda, M, K, B, s, C, 1, kslice, 0, st);
+  double* part = nullptr;
+  cudaError_t e = partial_buffer(static_cast<size_t>(nslices) * count, &part);
+  if (e != cudaSuccess) return e;
+  e = launch_slices(trans, A, lda, M, K, B, s, part, nslices, kslice, count, st);
+  if (e != cudaSuccess) return e;
+  const unsigned rg = static_cast<unsigned>(std::min<int64_t>((count + 255) / 256, 8 * sm_count()));
+  sum_slices<<<rg, 256, 0, st>>>(part, nslices, count, C);
+  return cudaGetLastError();
+}
+
+// ---- host-resident A: per-device staging, copy stream and events ----------------------------
+
+struct HostStream {
+  double* stage[2] = {nullptr, nullptr};
+  size_t stage_doubles = 0;
+  double* zpart = nullptr;
+  size_t zpart_doubles = 0;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+};
+std::mutex g_host_mutex;
+std::vector<HostStream> g_host;
+
+cudaError_t grow(double** p, size_t* have, size_t want) {
+  if (*have >= want) return cudaSuccess;
+  if (*p) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+  }
+  cudaError_t e = cudaMalloc(p, want * sizeof(double));
+  if (e == cudaSuccess) *have = want;
+  return e;
+}
+
+cudaError_t host_stream(size_t stage_doubles, size_t zpart_doubles, HostStream** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_host_mutex);
+  if (static_cast<int>(g_host.size()) <= dev) g_host.resize(dev + 1);
+  HostStream& h = g_host[dev];
+  if (!h.copy) {
+    e = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&h.copied[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.consumed[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  size_t have0 = h.stage_doubles, have1 = h.stage_doubles;
+  e = grow(&h.stage[0], &have0, stage_doubles);
+  if (e == cudaSuccess) e = grow(&h.stage[1], &have1, stage_doubles);
+  if (e != cudaSuccess) return e;
+  h.stage_doubles = std::min(have0, have1);
+  e = grow(&h.zpart, &h.zpart_doubles, zpart_doubles);
+  if (e != cudaSuccess) return e;
+  *out = &h;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,
                                     const double* Ps, int s, double* Y, double* Z,
                                     cudaStream_t st) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms <= 0) sms = 152;
-  const int64_t mt = (N + BM - 1) / BM, nt = (s + BN - 1) / BN;
-  const int slices = reduction_slices(N, mt * nt, sms);
-  const int64_t kslice = ((N + slices - 1) / slices + BK - 1) / BK * BK;
-  const int nslices = static_cast<int>((N + kslice - 1) / kslice);
-  const dim3 grid(static_cast<unsigned>(mt), static_cast<unsigned>(nt), static_cast<unsigned>(nslices));
+  cudaError_t e = product(false, A, lda, N, N, Om, s, Y, st);
+  if (e != cudaSuccess) return e;
+  return product(true, A, lda, N, N, Ps, s, Z, st);
+}
+
+cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, const double* Om,
+                                   const double* Ps, int s, double* Y, double* Z,
+                                   cudaStream_t st) {
+  // row blocks of ~N/8 rows (a multiple of the 64-row tile), at most 2 GiB of staging each
+  int64_t nb = ((N + 7) / 8 + BM - 1) / BM * BM;
+  const int64_t cap = std::max<int64_t>(BM, (int64_t(1) << 28) / std::max<int64_t>(1, N) / BM * BM);
+  nb = std::max<int64_t>(BM, std::min(nb, cap));
+  nb = std::min(nb, N);
+  const int64_t nblocks = (N + nb - 1) / nb;
+  int zs = 0;                                          // Z slices per block
+  int64_t zk = 0;
+  plan_slices(N, nb, s, &zs, &zk);
   const int64_t count = N * s;
-  double* part = nullptr;
-  if (nslices > 1) {
-    cudaError_t e = partial_buffer(static_cast<size_t>(nslices) * count, &part);
-    if (e != cudaSuccess) return e;
-  }
-  const unsigned rg = static_cast<unsigned>(std::min<int64_t>((count + 255) / 256, 8 * sms));
-  for (int which = 0; which < 2; ++which) {
-    double* C = which ? Z : Y;
-    double* dst = nslices > 1 ? part : C;
-    if (which == 0)
-      sample_gemm_f64<false><<<grid, THREADS, 0, st>>>(A, lda, N, Om, s, dst, kslice, count);
-    else
-      sample_gemm_f64<true><<<grid, THREADS, 0, st>>>(A, lda, N, Ps, s, dst, kslice, count);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (nslices > 1) {
-      sum_slices<<<rg, 256, 0, st>>>(part, nslices, count, C);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+  HostStream* h = nullptr;
+  cudaError_t e = host_stream(static_cast<size_t>(nb) * N,
+                              static_cast<size_t>(nblocks) * zs * count, &h);
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(h->start, st);                   // the stages are free once st is here
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy, h->start, 0);
+  for (int64_t b = 0; b < nblocks && e == cudaSuccess; ++b) {
+    const int slot = static_cast<int>(b & 1);
+    const int64_t r0 = b * nb, rows = std::min(nb, N - r0);
+    if (b >= 2) e = cudaStreamWaitEvent(h->copy, h->consumed[slot], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(h->stage[slot], N * sizeof(double), A + r0 * lda, lda * sizeof(double),
+                            N * sizeof(double), rows, cudaMemcpyHostToDevice, h->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(h->copied[slot], h->copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->copied[slot], 0);
+    if (e == cudaSuccess) e = product(false, h->stage[slot], N, rows, N, Om, s, Y + r0 * s, st);
+    if (e == cudaSuccess) {
+      // zs slices for every block (a short last block leaves some empty: they write zeros)
+      const int64_t zkb = ((rows + zs - 1) / zs + BK - 1) / BK * BK;
+      double* zb = h->zpart + static_cast<size_t>(b) * zs * count;
+      e = launch_slices(true, h->stage[slot], N, N, rows, Ps + r0 * s, s, zb, zs, zkb, count, st);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(h->consumed[slot], st);
   }
-  return cudaSuccess;
+  if (e != cudaSuccess) return e;
+  const unsigned rg = static_cast<unsigned>(std::min<int64_t>((count + 255) / 256, 8 * sm_count()));
+  sum_slices<<<rg, 256, 0, st>>>(h->zpart, static_cast<int>(nblocks) * zs, count, Z);
+  return cudaGetLastError();
 }
 
 }  // namespace hbs

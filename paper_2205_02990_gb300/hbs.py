@@ -137,11 +137,15 @@ def hbs_draw_gaussian(N, s, stream_id, seed, out):
 
 
 def _operator(A, N):
-    """(ctypes operator, keep-alive) for a dense CUDA float64 tensor or a callable black box."""
+    """(ctypes operator, keep-alive) for a dense matrix or a callable black box. A dense A is a
+    CUDA tensor, or a page-locked (pinned) CPU float64 tensor, which the FP64 products stream
+    through the device."""
     if isinstance(A, torch.Tensor):
-        if (not A.is_cuda or A.dtype not in (torch.float64, torch.float32) or A.dim() != 2
+        where_ok = A.is_cuda or (A.dtype == torch.float64 and A.is_pinned())
+        if (not where_ok or A.dtype not in (torch.float64, torch.float32) or A.dim() != 2
                 or A.shape[0] != A.shape[1] or A.stride(1) != 1 or A.stride(0) < A.shape[0]):
-            raise TypeError("A must be a square row-major CUDA float64 or float32 matrix")
+            raise TypeError("A must be a square row-major CUDA float64 or float32 matrix, "
+                            "or a pinned CPU float64 matrix")
         N = A.shape[0]
         dt = HBS_F64 if A.dtype == torch.float64 else HBS_F32
         op = _Operator(N=N, dtype=dt, A=A.data_ptr(), lda=A.stride(0), fn=MATMAT_FN(), user=None)
@@ -163,7 +167,8 @@ def _operator(A, N):
 def hbs_sample(A, s, seed, Omega, Psi, Y, Z, precision=HBS_PREC_FP64, N=None):
     """Draw Omega, Psi and form Y = A Omega, Z = A^* Psi.
 
-    ``A`` is a dense CUDA float64 tensor (N x N, row-major) or a callable
+    ``A`` is a dense CUDA float64 tensor (N x N, row-major; a pinned CPU float64 tensor is
+    streamed through the device in row blocks) or a callable
     ``fn(trans, X, Out)`` that writes A X (trans = 0) or A^* X (trans = 1) into ``Out``
     (both N x s CUDA float64 tensors) on the current stream.
     """
