@@ -119,7 +119,7 @@ struct hbs_handle {
 
 namespace {
 
-int check_problem(const hbs_problem& p, int idx) {
+int check_problem(const hbs_problem& p, int idx, bool fp32_nodes) {
   if (p.N < 1 || p.r < 1 || p.s < 1 || p.leaf_max < 1)
     return fail(HBS_ERR_ARG, "problem %d: N, r, s, leaf_max must be positive", idx);
   if (!p.Omega || !p.Psi || !p.Y || !p.Z)
@@ -143,8 +143,7 @@ int check_problem(const hbs_problem& p, int idx) {
   if (p.s > hbs::kMaxS)
     return fail(HBS_ERR_UNSUPPORTED, "problem %d: s = %d exceeds %d", idx, p.s, hbs::kMaxS);
   const int64_t nmax = (L == 0) ? p.N : std::max<int64_t>(2 * p.r, size[int64_t(1) << L]);
-  if (hbs::side_smem_doubles(int(nmax), p.s) * sizeof(double) > hbs::kMaxNodeSmemBytes ||
-      hbs::finish_smem_reals(int(nmax), p.r) * sizeof(double) > hbs::kMaxNodeSmemBytes)
+  if (hbs::node_smem_bytes(int(nmax), p.r, p.s, fp32_nodes) > hbs::kMaxNodeSmemBytes)
     return fail(HBS_ERR_UNSUPPORTED, "problem %d: node tile of %lld x %d exceeds shared memory",
                 idx, (long long)nmax, p.s);
   return HBS_OK;
@@ -426,7 +425,8 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
       precision != HBS_PREC_MIXED_BF16X6 && precision != HBS_PREC_FP64_TC)
     return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: unknown precision %d", precision);
   for (int i = 0; i < batch; ++i) {
-    const int rc = check_problem(probs[i], i);
+    const int rc = check_problem(probs[i], i, precision == HBS_PREC_MIXED_BF16X3 ||
+                                                   precision == HBS_PREC_MIXED_BF16X6);
     if (rc != HBS_OK) return rc;
   }
   auto* h = new hbs_handle();

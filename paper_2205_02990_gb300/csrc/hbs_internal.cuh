@@ -47,7 +47,7 @@ struct GemmTask {
 
 // Shared memory of the sweep kernels for a node of n rows (sweep.cu).
 size_t side_smem_doubles(int n, int s);
-size_t finish_smem_reals(int n, int r);
+size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes);   // largest sweep-kernel tile
 constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
 

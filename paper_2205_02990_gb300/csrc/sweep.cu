@@ -277,21 +277,25 @@ __global__ void __launch_bounds__(THREADS, 2)
 
 // U = col(Y P, r) (side 0) or V = col(Z Q, r) (side 1): unpivoted Householder QR, first r
 // columns formed explicitly.
-template <int NS>
+// Real = float in the mixed precisions (the sample block converted once on load; the basis is
+// stored as FP64).
+template <class Real, int NS>
 __global__ void __launch_bounds__(THREADS)
     node_bases(const NodeTask* __restrict__ tasks, int* status) {
-  extern __shared__ double bsm[];
+  extern __shared__ __align__(16) unsigned char bsm_bytes[];
+  Real* bsm = reinterpret_cast<Real*>(bsm_bytes);
   const NodeTask tk = tasks[blockIdx.x];
   if (tk.is_root) return;
   const int n = tk.n, r = tk.r;
   const int ldX = n + 1;
-  double* XT = bsm;                                    // r x ldX: (Y P)^* or (Z Q)^*
-  double* tau2 = XT + static_cast<size_t>(r) * ldX;    // r
+  Real* XT = bsm;                                      // r x ldX: (Y P)^* or (Z Q)^*
+  Real* tau2 = XT + static_cast<size_t>(r) * ldX;      // r
   const double* X = blockIdx.y ? tk.XZ : tk.XY;
-  for (int e = threadIdx.x; e < n * r; e += THREADS) XT[(e % r) * ldX + e / r] = X[e];
+  for (int e = threadIdx.x; e < n * r; e += THREADS)
+    XT[(e % r) * ldX + e / r] = static_cast<Real>(X[e]);
   __syncthreads();
-  lq_factor<double>(XT, ldX, r, n, tau2, nullptr, status);
-  form_basis<double, NS>(XT, ldX, tau2, r, n, blockIdx.y ? tk.V : tk.U, r);
+  lq_factor<Real>(XT, ldX, r, n, tau2, nullptr, status);
+  form_basis<Real, NS>(XT, ldX, tau2, r, n, blockIdx.y ? tk.V : tk.U, r);
 }
 
 // Columns [j0, j0 + nb) of P = U^* WY and Q = U^* WZ^*, into the spent XZ and XY (r x n).
@@ -407,130 +411,157 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-// FP32 finish with every operand staged in shared memory once. On GB300 a conversion from FP64
-// runs at the FP64 rate, so converting each operand inside the product loops (one conversion per
-// FMA) would make this kernel as slow as its FP64 twin; staged, a node converts each input entry
-// once (4 n s + 2 n^2 + 2 n r values) and the loops run on FP32 data in shared memory.
-template <int NS>
+// Small FP32 product in shared memory with a register tile per thread: for i < M, j < N,
+// C(i, j) = init(i, j) + sum_k a(i, k) b(k, j), stored by out(i, j, value). A warp takes a tile
+// of TM rows and 32 TN columns, lane l the columns l, l + 32, ...: a(i, k) is the same for the
+// whole warp (one broadcast) and b(k, j) is read by consecutive lanes (no bank conflicts), so
+// each k costs TM + TN shared loads per warp for 32 TM TN multiply-adds.
+template <int TM, int TN, class FA, class FB, class FI, class FO>
+__device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI init, FO out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tn = (N + 32 * TN - 1) / (32 * TN), tm = (M + TM - 1) / TM;
+  for (int t = warp; t < tm * tn; t += THREADS / 32) {
+    const int i0 = (t / tn) * TM, j0 = (t % tn) * 32 * TN + lane;
+    float acc[TM][TN];
+#pragma unroll
+    for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < TN; ++jj)
+        acc[ii][jj] = (i0 + ii < M && j0 + 32 * jj < N) ? init(i0 + ii, j0 + 32 * jj) : 0.f;
+    for (int k = 0; k < K; ++k) {
+      float av[TM], bv[TN];
+#pragma unroll
+      for (int ii = 0; ii < TM; ++ii) av[ii] = a(min(i0 + ii, M - 1), k);
+#pragma unroll
+      for (int jj = 0; jj < TN; ++jj) bv[jj] = b(k, min(j0 + 32 * jj, N - 1));
+#pragma unroll
+      for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fmaf(av[ii], bv[jj], acc[ii][jj]);
+    }
+#pragma unroll
+    for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < TN; ++jj)
+        if (i0 + ii < M && j0 + 32 * jj < N) out(i0 + ii, j0 + 32 * jj, acc[ii][jj]);
+  }
+}
+
+// FP32 D products with every operand staged in shared memory once. On GB300 a conversion from
+// FP64 runs at the FP64 rate, so converting each operand inside the product loops (one
+// conversion per FMA) would make this kernel as slow as FP64 arithmetic; staged, a node converts
+// each input entry once. One CTA per node, after node_bases<float> has written U and V: D_tau
+// (stored as FP64), then U^* D and (D V)^* (r x n) into the spent XY and XZ for node_merge_f32.
 __global__ void __launch_bounds__(THREADS, 1)
-    node_finish_f32(const NodeTask* __restrict__ tasks, int* status) {
+    node_dchain_f32(const NodeTask* __restrict__ tasks) {
   extern __shared__ __align__(16) float fsm[];
   const NodeTask tk = tasks[blockIdx.x];
   if (tk.is_root) return;
-  const int n = tk.n, r = tk.r, s = tk.s;
+  const int n = tk.n, r = tk.r;
   const int ldX = n + 1, ldT = n + 1;
-  float* XT = fsm;                                     // r x ldX: col sample block, later G1 = U^* T2^*
-  float* Hs = XT + static_cast<size_t>(r) * ldX;       // r x n: U^*(T2^* - WY), later (D V)^*
-  float* tau2 = Hs + static_cast<size_t>(r) * n;       // r
-  float* Us = tau2 + r;                                // n x r
+  float* G1 = fsm;                                     // r x ldX: V^* WZ, later U^* D
+  float* Hs = G1 + static_cast<size_t>(r) * ldX;       // r x n: U^*(T2^* - WY), later (D V)^*
+  float* Us = Hs + static_cast<size_t>(r) * n;         // n x r
   float* Vs = Us + static_cast<size_t>(n) * r;         // n x r
   float* T2 = Vs + static_cast<size_t>(n) * r;         // n x ldT: (I - VV^*) WZ, later D
   float* WYs = T2 + static_cast<size_t>(n) * ldT;      // n x n
   float* WZs = WYs + static_cast<size_t>(n) * n;       // n x n
-  float* free0 = T2;                                   // staging area for the merge blocks
-  const size_t free_floats = static_cast<size_t>(n) * ldT + 2 * static_cast<size_t>(n) * n;
-
-  // ---- U = col(Y P, r), V = col(Z Q, r), kept in shared memory (and stored as FP64) ----
-  for (int side = 0; side < 2; ++side) {
-    const double* X = side ? tk.XZ : tk.XY;
-    for (int e = threadIdx.x; e < n * r; e += THREADS)
-      XT[(e % r) * ldX + e / r] = static_cast<float>(X[e]);
-    __syncthreads();
-    lq_factor<float>(XT, ldX, r, n, tau2, nullptr, status);
-    double* B = side ? tk.V : tk.U;
-    form_basis<float, NS>(XT, ldX, tau2, r, n, B, r);
-    __syncthreads();
-    float* Bs = side ? Vs : Us;
-    for (int e = threadIdx.x; e < n * r; e += THREADS) Bs[e] = static_cast<float>(B[e]);
+  for (int e = threadIdx.x; e < n * r; e += THREADS) {
+    Us[e] = static_cast<float>(tk.U[e]);
+    Vs[e] = static_cast<float>(tk.V[e]);
   }
   for (int e = threadIdx.x; e < n * n; e += THREADS) {
     WYs[e] = static_cast<float>(tk.WY[e]);
     WZs[e] = static_cast<float>(tk.WZ[e]);
   }
   __syncthreads();
-
-  // ---- D_tau (Eq. d_tau_formula) ----
-  float* G1 = XT;
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, j = e % n;
-    float acc = 0.f;
-    for (int i = 0; i < n; ++i) acc = fmaf(Vs[i * r + c], WZs[i * n + j], acc);
-    G1[c * ldX + j] = acc;
-  }
+  // G1 = V^* WZ (r x n)
+  tile_gemm<4, 1>(r, n, n, [&](int c, int i) { return Vs[i * r + c]; },
+                  [&](int i, int j) { return WZs[i * n + j]; }, [](int, int) { return 0.f; },
+                  [&](int c, int j, float v) { G1[c * ldX + j] = v; });
   __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += THREADS) {
-    const int i = e / n, j = e % n;
-    float acc = WZs[e];
-    for (int c = 0; c < r; ++c) acc = fmaf(-Vs[i * r + c], G1[c * ldX + j], acc);
-    T2[i * ldT + j] = acc;
-  }
+  // T2 = WZ - V G1 (n x n)
+  tile_gemm<8, 1>(n, n, r, [&](int i, int c) { return -Vs[i * r + c]; },
+                  [&](int c, int j) { return G1[c * ldX + j]; },
+                  [&](int i, int j) { return WZs[i * n + j]; },
+                  [&](int i, int j, float v) { T2[i * ldT + j] = v; });
   __syncthreads();
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, j = e % n;
-    float h2 = 0.f, ky = 0.f;
-    for (int i = 0; i < n; ++i) {
-      const float u = Us[i * r + c];
-      h2 = fmaf(u, T2[j * ldT + i], h2);
-      ky = fmaf(u, WYs[i * n + j], ky);
-    }
-    G1[c * ldX + j] = h2;
-    Hs[c * n + j] = h2 - ky;
-  }
+  // G1 = U^* T2^* (= U^* D), then Hs = G1 - U^* WY
+  tile_gemm<4, 1>(r, n, n, [&](int c, int i) { return Us[i * r + c]; },
+                  [&](int i, int j) { return T2[j * ldT + i]; }, [](int, int) { return 0.f; },
+                  [&](int c, int j, float v) { G1[c * ldX + j] = v; });
   __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += THREADS) {
-    const int i = e / n, j = e % n;
-    float acc = WYs[e];
-    for (int c = 0; c < r; ++c) acc = fmaf(Us[i * r + c], Hs[c * n + j], acc);
-    tk.D[e] = static_cast<double>(acc);
-    T2[i * ldT + j] = acc;
-  }
+  tile_gemm<4, 1>(r, n, n, [&](int c, int i) { return -Us[i * r + c]; },
+                  [&](int i, int j) { return WYs[i * n + j]; },
+                  [&](int c, int j) { return G1[c * ldX + j]; },
+                  [&](int c, int j, float v) { Hs[c * n + j] = v; });
+  __syncthreads();
+  // D = WY + U Hs (n x n), stored as FP64 and kept in T2
+  tile_gemm<8, 1>(n, n, r, [&](int i, int c) { return Us[i * r + c]; },
+                  [&](int c, int j) { return Hs[c * n + j]; },
+                  [&](int i, int j) { return WYs[i * n + j]; },
+                  [&](int i, int j, float v) {
+                    tk.D[static_cast<size_t>(i) * n + j] = static_cast<double>(v);
+                    T2[i * ldT + j] = v;
+                  });
+  __syncthreads();
+  // Hs = (D V)^* (r x n)
+  tile_gemm<4, 1>(r, n, n, [&](int c, int j) { return Vs[j * r + c]; },
+                  [&](int j, int i) { return T2[i * ldT + j]; }, [](int, int) { return 0.f; },
+                  [&](int c, int i, float v) { Hs[c * n + i] = v; });
   __syncthreads();
   for (int e = threadIdx.x; e < r * n; e += THREADS) {
     const int c = e / n, i = e % n;
-    float acc = 0.f;
-    for (int j = 0; j < n; ++j) acc = fmaf(T2[i * ldT + j], Vs[j * r + c], acc);
-    Hs[c * n + i] = acc;
+    tk.XY[e] = static_cast<double>(G1[c * ldX + i]);
+    tk.XZ[e] = static_cast<double>(Hs[e]);
+  }
+}
+
+// FP32 merges (Eq. omega_tau_and_y_tau): grid (node, chunk of kw columns, pass) as node_merge,
+// from U, V and the products U^* D, (D V)^* that node_dchain_f32 left in XY, XZ; the chunk, the
+// bases and the product are staged in shared memory as FP32.
+__global__ void __launch_bounds__(THREADS)
+    node_merge_f32(const NodeTask* __restrict__ tasks, int chunk) {
+  extern __shared__ __align__(16) float msf[];
+  const NodeTask tk = tasks[blockIdx.x];
+  if (tk.is_root) return;
+  const int n = tk.n, r = tk.r, s = tk.s;
+  const int k0 = blockIdx.y * chunk;
+  if (k0 >= s) return;
+  const int kw = min(chunk, s - k0);
+  const int pass = blockIdx.z;
+  const double* T = pass ? tk.Ps : tk.Om;
+  const double* S = pass ? tk.Z : tk.Y;
+  const double* Bt = pass ? tk.U : tk.V;               // reduces the test block
+  const double* Bs = pass ? tk.V : tk.U;               // reduces the sample block
+  const double* H = pass ? tk.XZ : tk.XY;              // (D V)^* or U^* D, r x n
+  double* outT = pass ? tk.Ps_p : tk.Om_p;
+  double* outS = pass ? tk.Z_p : tk.Y_p;
+  float* Ts = msf;                                     // n x kw
+  float* Ss = Ts + static_cast<size_t>(n) * kw;        // n x kw
+  float* Bts = Ss + static_cast<size_t>(n) * kw;       // n x r
+  float* Bss = Bts + static_cast<size_t>(n) * r;       // n x r
+  float* Hsm = Bss + static_cast<size_t>(n) * r;       // r x n
+  for (int e = threadIdx.x; e < n * kw; e += THREADS) {
+    const int i = e / kw, k = e % kw;
+    Ts[e] = static_cast<float>(T[static_cast<size_t>(i) * s + k0 + k]);
+    Ss[e] = static_cast<float>(S[static_cast<size_t>(i) * s + k0 + k]);
+  }
+  for (int e = threadIdx.x; e < n * r; e += THREADS) {
+    Bts[e] = static_cast<float>(Bt[e]);
+    Bss[e] = static_cast<float>(Bs[e]);
+    Hsm[e] = static_cast<float>(H[e]);
   }
   __syncthreads();
-
-  // ---- this node's rows of the parent's blocks, in column chunks staged as FP32 ----
-  // pass 0: Omega_p = V^* Omega_tau, Y_p = U^* Y_tau - (U^* D) Omega_tau
-  // pass 1: Psi_p = U^* Psi_tau,     Z_p = V^* Z_tau - (D V)^* Psi_tau
-  const int kc = static_cast<int>(min(static_cast<size_t>(s), free_floats / (2 * static_cast<size_t>(n))));
-  for (int pass = 0; pass < 2; ++pass) {
-    const double* T = pass ? tk.Ps : tk.Om;
-    const double* S = pass ? tk.Z : tk.Y;
-    const float* Bt = pass ? Us : Vs;                  // basis reducing the test block
-    const float* Bs = pass ? Vs : Us;                  // basis reducing the sample block
-    const float* Hm = pass ? Hs : G1;                  // U^* D or (D V)^*
-    const int ldH = pass ? n : ldX;
-    double* outT = pass ? tk.Ps_p : tk.Om_p;
-    double* outS = pass ? tk.Z_p : tk.Y_p;
-    for (int k0 = 0; k0 < s; k0 += kc) {
-      const int kw = min(kc, s - k0);
-      float* Ts = free0;                               // n x kw
-      float* Ss = free0 + static_cast<size_t>(n) * kw; // n x kw
-      __syncthreads();
-      for (int e = threadIdx.x; e < n * kw; e += THREADS) {
-        const int i = e / kw, k = e % kw;
-        Ts[e] = static_cast<float>(T[static_cast<size_t>(i) * s + k0 + k]);
-        Ss[e] = static_cast<float>(S[static_cast<size_t>(i) * s + k0 + k]);
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < r * kw; e += THREADS) {
-        const int c = e / kw, k = e % kw;
-        float t = 0.f, y = 0.f;
-        for (int i = 0; i < n; ++i) {
-          const float tv = Ts[i * kw + k];
-          t = fmaf(Bt[i * r + c], tv, t);
-          y = fmaf(Bs[i * r + c], Ss[i * kw + k], y);
-          y = fmaf(-Hm[c * ldH + i], tv, y);
-        }
-        outT[c * s + k0 + k] = static_cast<double>(t);
-        outS[c * s + k0 + k] = static_cast<double>(y);
-      }
-    }
-  }
+  tile_gemm<2, 1>(r, kw, n, [&](int c, int i) { return Bts[i * r + c]; },
+                  [&](int i, int k) { return Ts[i * kw + k]; }, [](int, int) { return 0.f; },
+                  [&](int c, int k, float v) { outT[c * s + k0 + k] = static_cast<double>(v); });
+  // U^* S - H T as one product over 2n: [Bs^*, -H] [S; T]
+  tile_gemm<2, 1>(r, kw, 2 * n,
+                  [&](int c, int i) { return i < n ? Bss[i * r + c] : -Hsm[c * n + i - n]; },
+                  [&](int i, int k) { return i < n ? Ss[i * kw + k] : Ts[(i - n) * kw + k]; },
+                  [](int, int) { return 0.f; },
+                  [&](int c, int k, float v) { outS[c * s + k0 + k] = static_cast<double>(v); });
 }
 
 template <class Kernel>
@@ -545,10 +576,6 @@ size_t side_smem_doubles(int n, int s) {
   return static_cast<size_t>(n) * (s + 1) + 2 * static_cast<size_t>(n);
 }
 
-size_t finish_smem_reals(int n, int r) {
-  return static_cast<size_t>(r) * (n + 1) + static_cast<size_t>(n) * (n + 1) +
-         static_cast<size_t>(r) * n + r;
-}
 
 size_t merge_smem_doubles(int n) { return 2 * static_cast<size_t>(n) * kMergeCols; }
 size_t bases_smem_doubles(int n, int r) { return static_cast<size_t>(r) * (n + 1) + r; }
@@ -560,9 +587,24 @@ size_t dblk_smem_doubles(int r, int nb) {
 // re-forms the r x r product R, r^2 n flops, against ~4 r n^2 / blocks of its own work).
 int dblk_blocks(int ntasks) { return std::max(1, std::min(8, (2 * 152) / std::max(1, ntasks))); }
 
-// FP32 finish: the FP64 finish's regions plus the staged U, V, WY, WZ (floats).
-size_t finish_f32_smem_floats(int n, int r) {
-  return finish_smem_reals(n, r) + 2 * static_cast<size_t>(n) * r + 2 * static_cast<size_t>(n) * n;
+// FP32 D products: G1, Hs, T2 and the staged U, V, WY, WZ (floats).
+size_t dchain_f32_smem_floats(int n, int r) {
+  return static_cast<size_t>(r) * (n + 1) + static_cast<size_t>(r) * n +
+         2 * static_cast<size_t>(n) * r + static_cast<size_t>(n) * (n + 1) +
+         2 * static_cast<size_t>(n) * n;
+}
+size_t merge_f32_smem_floats(int n, int r, int chunk) {
+  return 2 * static_cast<size_t>(n) * chunk + 3 * static_cast<size_t>(n) * r;
+}
+
+// The largest shared-memory tile the sweep kernels need for a node of n rows.
+size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes) {
+  const size_t d = sizeof(double), f = sizeof(float);
+  const size_t common = std::max(side_smem_doubles(n, s) * d, bases_smem_doubles(n, r) * d);
+  if (fp32_nodes)
+    return std::max({common, dchain_f32_smem_floats(n, r) * f,
+                     merge_f32_smem_floats(n, r, kMergeCols) * f});
+  return std::max({common, dblk_smem_doubles(r, n) * d, merge_smem_doubles(n) * d});
 }
 
 int side_row_splits(int ntasks, int n) {
@@ -599,14 +641,19 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
                                cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
   if (max_s > kMaxS) return cudaErrorInvalidValue;
+  // about four merge CTAs per SM in all; chunks of 8 .. 32 columns
+  const int want = std::max(1, (4 * 152) / (2 * ntasks));
+  const int chunk = std::max(8, std::min(kMergeCols, (max_s + want - 1) / want));
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
-  const size_t fin_bytes = fp32_finish ? finish_f32_smem_floats(max_n, max_r) * sizeof(float)
-                                       : bases_smem_doubles(max_n, max_r) * sizeof(double);
+  const size_t bases_bytes = bases_smem_doubles(max_n, max_r) *
+                             (fp32_finish ? sizeof(float) : sizeof(double));
   const int blocks = dblk_blocks(ntasks);
   const int nb = (max_n + blocks - 1) / blocks;
-  const size_t dblk_bytes = dblk_smem_doubles(max_r, nb) * sizeof(double);
-  const size_t merge_bytes = merge_smem_doubles(max_n) * sizeof(double);
-  if (side_bytes > kMaxNodeSmemBytes || fin_bytes > kMaxNodeSmemBytes ||
+  const size_t dblk_bytes = fp32_finish ? dchain_f32_smem_floats(max_n, max_r) * sizeof(float)
+                                        : dblk_smem_doubles(max_r, nb) * sizeof(double);
+  const size_t merge_bytes = fp32_finish ? merge_f32_smem_floats(max_n, max_r, chunk) * sizeof(float)
+                                         : merge_smem_doubles(max_n) * sizeof(double);
+  if (side_bytes > kMaxNodeSmemBytes || bases_bytes > kMaxNodeSmemBytes ||
       dblk_bytes > kMaxNodeSmemBytes || merge_bytes > kMaxNodeSmemBytes)
     return cudaErrorInvalidValue;
   const int splits = row_splits > 0 ? std::max(1, std::min(row_splits, std::max(1, max_n)))
@@ -620,55 +667,55 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
       e = cudaGetLastError();
     }
   };
-  auto finish = [&](auto kernel) {
-    e = allow_smem(kernel);
-    if (e == cudaSuccess) {
-      kernel<<<ntasks, THREADS, fin_bytes, st>>>(d_tasks, d_status);
-      e = cudaGetLastError();
-    }
-  };
   if (max_s <= 8 * G) side(node_side<8>);
   else if (max_s <= 16 * G) side(node_side<16>);
   else side(node_side<24>);
   if (e != cudaSuccess) return e;
-  // the finish kernel's register slots span the n <= s columns of a basis
+  // bases: one CTA per (node, side); the register slots span the n <= s columns of a basis
+  const dim3 bgrid(static_cast<unsigned>(ntasks), 2u);
+  auto bases = [&](auto kernel) {
+    e = allow_smem(kernel);
+    if (e == cudaSuccess) {
+      kernel<<<bgrid, THREADS, bases_bytes, st>>>(d_tasks, d_status);
+      e = cudaGetLastError();
+    }
+  };
   if (fp32_finish) {
-    if (max_n <= 8 * G) finish(node_finish_f32<8>);
-    else if (max_n <= 16 * G) finish(node_finish_f32<16>);
-    else finish(node_finish_f32<24>);
+    if (max_n <= 8 * G) bases(node_bases<float, 8>);
+    else if (max_n <= 16 * G) bases(node_bases<float, 16>);
+    else bases(node_bases<float, 24>);
   } else {
-    const dim3 bgrid(static_cast<unsigned>(ntasks), 2u);
-    auto bases = [&](auto kernel) {
-      e = allow_smem(kernel);
-      if (e == cudaSuccess) {
-        kernel<<<bgrid, THREADS, fin_bytes, st>>>(d_tasks, d_status);
-        e = cudaGetLastError();
-      }
-    };
-    if (max_n <= 8 * G) bases(node_bases<8>);
-    else if (max_n <= 16 * G) bases(node_bases<16>);
-    else bases(node_bases<24>);
-    if (e != cudaSuccess) return e;
-    const dim3 dgrid(static_cast<unsigned>(ntasks), static_cast<unsigned>(blocks));
-    node_dblk_a<<<dgrid, THREADS, 0, st>>>(d_tasks, nb);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = allow_smem(node_dblk_b);
-    if (e != cudaSuccess) return e;
-    node_dblk_b<<<dgrid, THREADS, dblk_bytes, st>>>(d_tasks, nb);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = allow_smem(node_merge);
-    if (e != cudaSuccess) return e;
-    // about four CTAs per SM in all; chunks of 8 .. 32 columns
-    const int want = (4 * 152) / (2 * ntasks);
-    const int chunk = std::max(8, std::min(kMergeCols, (max_s + std::max(1, want) - 1) / std::max(1, want)));
-    const dim3 merge_grid(static_cast<unsigned>(ntasks),
-                          static_cast<unsigned>((max_s + chunk - 1) / chunk), 2u);
-    node_merge<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
-    e = cudaGetLastError();
+    if (max_n <= 8 * G) bases(node_bases<double, 8>);
+    else if (max_n <= 16 * G) bases(node_bases<double, 16>);
+    else bases(node_bases<double, 24>);
   }
-  return e;
+  if (e != cudaSuccess) return e;
+  const dim3 merge_grid(static_cast<unsigned>(ntasks),
+                        static_cast<unsigned>((max_s + chunk - 1) / chunk), 2u);
+  if (fp32_finish) {
+    e = allow_smem(node_dchain_f32);
+    if (e != cudaSuccess) return e;
+    node_dchain_f32<<<ntasks, THREADS, dblk_bytes, st>>>(d_tasks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = allow_smem(node_merge_f32);
+    if (e != cudaSuccess) return e;
+    node_merge_f32<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
+    return cudaGetLastError();
+  }
+  const dim3 dgrid(static_cast<unsigned>(ntasks), static_cast<unsigned>(blocks));
+  node_dblk_a<<<dgrid, THREADS, 0, st>>>(d_tasks, nb);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = allow_smem(node_dblk_b);
+  if (e != cudaSuccess) return e;
+  node_dblk_b<<<dgrid, THREADS, dblk_bytes, st>>>(d_tasks, nb);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = allow_smem(node_merge);
+  if (e != cudaSuccess) return e;
+  node_merge<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
+  return cudaGetLastError();
 }
 
 }  // namespace hbs
