@@ -24,30 +24,33 @@
 namespace hbs {
 namespace {
 
-constexpr int BM = 64, BN = 128, BK = 16, THREADS = 256;
+constexpr int BM = 64, BN = 128, BK = 16, THREADS = 256;   // BN: widest column tile
 constexpr int ASTRIDE = BM + 1;   // padded so that the transposing stores of op(A) = A hit
                                   // distinct banks
 
-template <bool TRANS>
+// TJ = columns per thread: the CTA's column tile is 16 TJ wide (TJ = 8 for s > 112, fewer for
+// narrower s, so that s = 90 or s = 30 does not pad to 128 columns).
+template <bool TRANS, int TJ>
 __global__ void __launch_bounds__(THREADS)
     sample_gemm_f64(const double* __restrict__ A, int64_t lda, int64_t M, int64_t K,
                     const double* __restrict__ B, int s, double* __restrict__ C, int64_t kslice,
                     int64_t ldc_split) {
+  constexpr int TBN = 16 * TJ;
   __shared__ double As[BK][ASTRIDE];   // As[k][m] = op(A)[m0 + m][k0 + k]
-  __shared__ double Bs[BK][BN];        // Bs[k][c] = B[k0 + k][c0 + c]
+  __shared__ double Bs[BK][TBN];       // Bs[k][c] = B[k0 + k][c0 + c]
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
-  const int c0 = blockIdx.y * BN;
+  const int c0 = blockIdx.y * TBN;
   const int64_t kbeg = static_cast<int64_t>(blockIdx.z) * kslice;
   const int64_t kend = min(K, kbeg + kslice);
   C += static_cast<int64_t>(blockIdx.z) * ldc_split;        // this slice's partial (or C itself)
 
-  double acc[4][8];
+  double acc[4][TJ];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TJ; ++j) acc[i][j] = 0.0;
 
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     // op(A) tile: BK x BM = 1024 doubles, 4 per thread
@@ -64,11 +67,11 @@ __global__ void __launch_bounds__(THREADS)
         As[k][m] = (gm < M && gk < kend) ? A[gk * lda + gm] : 0.0;
       }
     }
-    // B tile: BK x BN = 2048 doubles, 8 per thread
+    // B tile: BK x TBN doubles, TJ per thread
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < TJ; ++e) {
       const int idx = tid + e * THREADS;
-      const int c = idx % BN, k = idx / BN;
+      const int c = idx % TBN, k = idx / TBN;
       const int64_t gk = k0 + k;
       const int gc = c0 + c;
       Bs[k][c] = (gk < kend && gc < s) ? B[gk * s + gc] : 0.0;
@@ -76,15 +79,15 @@ __global__ void __launch_bounds__(THREADS)
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[8];
+      double a[4], b[TJ];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = Bs[k][tx + 16 * j];
+      for (int j = 0; j < TJ; ++j) b[j] = Bs[k][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(THREADS)
     const int64_t gm = m0 + ty * 4 + i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < TJ; ++j) {
       const int gc = c0 + tx + 16 * j;
       if (gc < s) C[gm * s + gc] = acc[i][j];
     }
@@ -166,22 +169,43 @@ int sm_count() {
   return sms > 0 ? sms : 152;
 }
 
+// Columns per thread of the product's tile: 16 TJ >= s up to TJ = 8 (wider s: tiles of 128).
+int col_per_thread(int s) { return std::min(8, std::max(1, (s + 15) / 16)); }
+
 // Slices of the reduction and their length (a multiple of BK) for an M x K product.
 void plan_slices(int64_t M, int64_t K, int s, int* nslices, int64_t* kslice) {
-  const int64_t tiles = ((M + BM - 1) / BM) * ((s + BN - 1) / BN);
+  const int tbn = 16 * col_per_thread(s);
+  const int64_t tiles = ((M + BM - 1) / BM) * ((s + tbn - 1) / tbn);
   const int slices = reduction_slices(K, tiles, sm_count());
   *kslice = ((K + slices - 1) / slices + BK - 1) / BK * BK;
   *nslices = static_cast<int>((K + *kslice - 1) / *kslice);
 }
 
 // Launches C (+ z * ldc) = the slices of op(A) B; C is M x s, slice z starts at C + z * ldc.
+template <int TJ>
+void launch_tj(bool trans, const dim3& grid, cudaStream_t st, const double* A, int64_t lda,
+               int64_t M, int64_t K, const double* B, int s, double* C, int64_t kslice,
+               int64_t ldc) {
+  if (trans) sample_gemm_f64<true, TJ><<<grid, THREADS, 0, st>>>(A, lda, M, K, B, s, C, kslice, ldc);
+  else sample_gemm_f64<false, TJ><<<grid, THREADS, 0, st>>>(A, lda, M, K, B, s, C, kslice, ldc);
+}
+
 cudaError_t launch_slices(bool trans, const double* A, int64_t lda, int64_t M, int64_t K,
                           const double* B, int s, double* C, int nslices, int64_t kslice,
                           int64_t ldc, cudaStream_t st) {
-  const dim3 grid(static_cast<unsigned>((M + BM - 1) / BM), static_cast<unsigned>((s + BN - 1) / BN),
+  const int tj = col_per_thread(s), tbn = 16 * tj;
+  const dim3 grid(static_cast<unsigned>((M + BM - 1) / BM), static_cast<unsigned>((s + tbn - 1) / tbn),
                   static_cast<unsigned>(nslices));
-  if (trans) sample_gemm_f64<true><<<grid, THREADS, 0, st>>>(A, lda, M, K, B, s, C, kslice, ldc);
-  else sample_gemm_f64<false><<<grid, THREADS, 0, st>>>(A, lda, M, K, B, s, C, kslice, ldc);
+  switch (tj) {
+    case 1: launch_tj<1>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 2: launch_tj<2>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 3: launch_tj<3>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 4: launch_tj<4>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 5: launch_tj<5>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 6: launch_tj<6>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 7: launch_tj<7>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    default: launch_tj<8>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+  }
   return cudaGetLastError();
 }
 
