@@ -74,6 +74,15 @@ def test_plan_rejects_on_host(lib, N, r, s, leaf, code):
     assert len(lib.hbs_last_error()) > 0
 
 
+def test_plan_rejects_tiles_beyond_shared_memory_per_precision(lib):
+    # leaves of 120 rows with r = 40, s = 160: the FP64 kernels' tiles fit in 227 KB of shared
+    # memory, the FP32 D products' staged tile (U, V, WY, WZ, T2, ...) does not
+    arr = (type(_problem(1, 1, 1, 1)) * 1)(_problem(1920, 40, 160, 120))
+    h = ctypes.c_void_p()
+    assert lib.hbs_plan(1, arr, 2, ctypes.byref(h)) == -8
+    assert not h.value and "shared memory" in lib.hbs_last_error().decode()
+
+
 def test_null_arguments_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.hbs_plan(1, None, 0, ctypes.byref(h)) == -1
