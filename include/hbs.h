@@ -104,8 +104,8 @@ typedef struct {
 } hbs_operator;
 
 /* Precision of the products (hbs_sample, hbs_sample_products): HBS_PREC_FP64 needs a dense A in
- * HBS_F64 or a callback; the mixed precisions need a dense A in HBS_F32 with lda a multiple of
- * 4 and s <= 256; HBS_PREC_FP64_TC needs a dense A in HBS_F64 (any lda >= N), s <= 256 and
+ * HBS_F64 or a callback; the mixed precisions need a dense A in HBS_F32, 16-byte aligned, with
+ * lda a multiple of 4 and s <= 256; HBS_PREC_FP64_TC needs a dense A in HBS_F64 (any lda >= N), s <= 256 and
  * N <= 2^20. All keep Omega, Psi, Y, Z in FP64. */
 
 /* Randomized samples (Algorithm 2, first block): draws Omega (stream 0) and Psi (stream 1)

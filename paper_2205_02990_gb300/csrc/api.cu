@@ -342,8 +342,10 @@ static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, 
   } else {
     if (!op->A || op->dtype != HBS_F32)
       return fail(HBS_ERR_UNSUPPORTED, "%s: mixed products need a dense FP32 A", who);
-    if (op->lda % 4 != 0 || s > 256 || op->N > (int64_t(1) << 30))
-      return fail(HBS_ERR_UNSUPPORTED, "%s: mixed products need lda %% 4 == 0 and s <= 256", who);
+    if (op->lda % 4 != 0 || s > 256 || op->N > (int64_t(1) << 30) ||
+        reinterpret_cast<uintptr_t>(op->A) % 16 != 0)
+      return fail(HBS_ERR_UNSUPPORTED,
+                  "%s: mixed products need a 16-byte aligned A, lda %% 4 == 0 and s <= 256", who);
   }
   return HBS_OK;
 }

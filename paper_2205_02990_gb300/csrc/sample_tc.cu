@@ -16,14 +16,18 @@
 // memory, while the tensor core fills the other accumulator of a ping-pong pair. The running
 // sum goes out as FP64; reduction splits exist only to balance the grid and are summed in FP64.
 //
-// CTA (320 threads, one per SM): warp 0 issues TMA loads (the FP32 A tile, unswizzled, and the
-// Q pre-split B tiles, 128-byte swizzled); warp 1 owns the tensor memory and one thread issues
-// tcgen05.mma (M = 128, N = BN <= 128, K = 16 per instruction); warps 2-5 split the FP32 A tile
-// into P bf16 tiles written in the 128-byte-swizzled K-major layout the MMA reads (transposing
-// it on the way for Z = A^* Psi); warps 6-9 drain the accumulators (tcgen05.ld / tcgen05.st)
-// and write the result. Tensor memory: two accumulators, hi, lo (4 x 128 columns).
-// mbarriers hand buffers between the roles; every wait is bounded in time and sets the
-// timeout bit of the status word instead of hanging.
+// CTA (448 threads, one per SM): warp 0 issues the TMA loads of the Q pre-split B tiles
+// (128-byte swizzled); warp 1 owns the tensor memory and one thread issues tcgen05.mma
+// (M = 128, N = BN <= 128, K = 16 per instruction); warps 2-9 read the FP32 A tile straight
+// from global memory (the next tile held in registers, the two after it prefetched into L2)
+// and write its P bf16 slices in the 128-byte-swizzled K-major layout the MMA reads
+// (transposing it on the way for Z = A^* Psi); warps 10-13 drain the accumulators
+// (tcgen05.ld / tcgen05.st) and write the result. The operand stages (P A slices + Q B slices)
+// form a ring of SO buffers (2 for bf16x6, 3 for bf16x3), so splitting the next tile overlaps
+// the current MMAs. Tensor memory: two accumulators, hi, lo (4 x 128 columns). mbarriers hand
+// buffers between the roles; every wait is bounded in time and sets the timeout bit of the
+// status word instead of hanging. (Measured: 4 converter warps leave the MMAs waiting for
+// slices; 8 drain warps next to 8 converters spill registers; this split is the fastest.)
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -37,37 +41,84 @@
 namespace hbs {
 namespace {
 
-constexpr int kTcThreads = 320;
+constexpr int kConvWarps = 8;                 // FP32 A -> bf16 slices
+constexpr int kDrainWarps = 4;                // per quarter of tensor-memory lanes: kDrainWarps / 4
+constexpr int kDrainParts = kDrainWarps / 4;  // column chunks c of a warp: c % kDrainParts == part
+constexpr int kTcThreads = 64 + 32 * (kConvWarps + kDrainWarps);
 constexpr int BM = 128;                       // MMA M: rows of C per CTA
 constexpr int BK = 64;                        // reduction columns per stage (128 B of bf16)
-constexpr int kStageABytes = BM * BK * 4;     // FP32 A tile
 constexpr int kSliceABytes = BM * BK * 2;     // one bf16 slice of the A tile
-// Split one FP32 A tile (staging, TMA layout) into P bf16 tiles in the K-major 128-byte
-// swizzled layout: row m at byte m*128, 16-byte chunk c (columns 8c..8c+7) at chunk c ^ (m%8).
-template <int P, bool TRANS>
-__device__ __forceinline__ void split_tile(const float* st, uint8_t* slices, int ct) {
+constexpr int kUnitsPerThread = BM * BK / 8 / (32 * kConvWarps);   // (row, 8-column) units
+// One converter thread's units of the A tile (rows m0.., reduction columns k0..): unit u is
+// (row m, 8-column chunk c) of op(A); the thread holds its 8 FP32 values. Y = A Omega reads
+// A[m0 + m][k0 + 8c ..] (8 lanes cover one 256-byte row); Z = A^* Psi reads A[k0 + 8c + e][m0 + m]
+// (32 lanes read 32 consecutive m of one row of A). Entries outside M x K read as zero.
+template <bool TRANS>
+__device__ __forceinline__ void load_units(const float* __restrict__ A, int64_t lda, int M, int K,
+                                           int m0, int k0, int ct,
+                                           float (&v)[kUnitsPerThread][8]) {
 #pragma unroll
-  for (int it = 0; it < 8; ++it) {
-    const int idx = ct + 128 * it;
-    int m, c;
-    float v[8];
-    if (!TRANS) {             // staging [m][k]: 8 lanes read one 256-byte row
-      c = idx & 7;
-      m = idx >> 3;
-      const float4 lo = *reinterpret_cast<const float4*>(st + m * BK + 8 * c);
-      const float4 hi = *reinterpret_cast<const float4*>(st + m * BK + 8 * c + 4);
-      v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-      v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-    } else {                  // staging [k][m]: a warp reads 32 consecutive m
-      m = idx & (BM - 1);
-      c = idx >> 7;
+  for (int it = 0; it < kUnitsPerThread; ++it) {
+    const int u = ct + 32 * kConvWarps * it;
+    if (!TRANS) {
+      const int m = u >> 3, c = u & 7;
+      const int64_t gm = m0 + m, gk = k0 + 8 * c;
+      if (gm < M && gk + 8 <= K) {
+        const float4* q = reinterpret_cast<const float4*>(A + gm * lda + gk);
+        const float4 lo = q[0], hi = q[1];
+        v[it][0] = lo.x; v[it][1] = lo.y; v[it][2] = lo.z; v[it][3] = lo.w;
+        v[it][4] = hi.x; v[it][5] = hi.y; v[it][6] = hi.z; v[it][7] = hi.w;
+      } else {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = st[(8 * c + e) * BM + m];
+        for (int e = 0; e < 8; ++e) v[it][e] = (gm < M && gk + e < K) ? A[gm * lda + gk + e] : 0.f;
+      }
+    } else {
+      const int m = u & (BM - 1), c = u >> 7;
+      const int64_t gm = m0 + m;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t gk = k0 + 8 * c + e;
+        v[it][e] = (gm < M && gk < K) ? A[gk * lda + gm] : 0.f;
+      }
     }
+  }
+}
+
+// Brings the A tile at (m0, k0) towards L2 ahead of its loads: its 256 lines of 128 bytes
+// (128 rows of 256 B for Y; 64 rows of A of 512 B for Z) spread over the converter threads.
+template <bool TRANS>
+__device__ __forceinline__ void prefetch_tile(const float* A, int64_t lda, int M, int K, int m0,
+                                              int k0, int ct) {
+#pragma unroll
+  for (int l = ct; l < 256; l += 32 * kConvWarps) {
+    int64_t row, col;
+    if (!TRANS) {
+      row = m0 + (l >> 1);
+      col = k0 + 32 * (l & 1);
+      if (row >= M || col >= K) continue;
+    } else {
+      row = k0 + (l >> 2);
+      col = m0 + 32 * (l & 3);
+      if (row >= K || col >= M) continue;
+    }
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(A + row * lda + col));
+  }
+}
+
+// Splits the units into P bf16 slices in the K-major 128-byte swizzled layout: row m at byte
+// m*128, 16-byte chunk c (columns 8c..8c+7) at chunk c ^ (m%8).
+template <int P, bool TRANS>
+__device__ __forceinline__ void store_units(const float (&v)[kUnitsPerThread][8], uint8_t* slices,
+                                            int ct) {
+#pragma unroll
+  for (int it = 0; it < kUnitsPerThread; ++it) {
+    const int u = ct + 32 * kConvWarps * it;
+    const int m = TRANS ? (u & (BM - 1)) : (u >> 3);
+    const int c = TRANS ? (u >> 7) : (u & 7);
     uint32_t w[P][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      float x0 = v[2 * e], x1 = v[2 * e + 1];
+      float x0 = v[it][2 * e], x1 = v[it][2 * e + 1];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
@@ -87,6 +138,8 @@ __device__ __forceinline__ void split_tile(const float* st, uint8_t* slices, int
 }
 
 struct TcArgs {
+  const float* A;  // FP32 A, row-major, lda % 4 == 0
+  int64_t lda;
   int M, K;        // rows of C, reduction length
   int BN;          // columns per CTA (multiple of 32, <= 128); blockIdx.z picks the column tile
   int BNt;         // padded columns of the whole product (BN x column tiles)
@@ -95,23 +148,19 @@ struct TcArgs {
   int* status;
 };
 
-template <int P, int Q, bool TRANS, int SA, int SO, int DR>
+template <int P, int Q, bool TRANS, int SO, int DR>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    sliced_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   TcArgs a) {
+    sliced_gemm_tc(const __grid_constant__ CUtensorMap tmB, TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   if (aborted(a.status)) return;              // a CTA of this or an earlier launch timed out
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int BN = a.BN;
   const int slice_b_bytes = BN * 128;
-  uint8_t* stA = smem;                                           // SA FP32 staging tiles
-  uint8_t* opA = stA + SA * kStageABytes;                        // SO x P bf16 A slices
+  uint8_t* opA = smem;                                           // SO x P bf16 A slices
   uint8_t* opB = opA + SO * P * kSliceABytes;                    // SO x Q bf16 B slices
-  uint64_t* a_full = reinterpret_cast<uint64_t*>(opB + SO * Q * slice_b_bytes);
-  uint64_t* a_empty = a_full + SA;
-  uint64_t* b_full = a_empty + SA;
-  uint64_t* o_empty = b_full + SO;
-  uint64_t* a_ready = o_empty + SO;
+  uint64_t* b_full = reinterpret_cast<uint64_t*>(opB + SO * Q * slice_b_bytes);
+  uint64_t* o_empty = b_full + SO;                               // the stage's MMAs are done
+  uint64_t* a_ready = o_empty + SO;                              // the stage's A slices written
   uint64_t* acc_full = a_ready + SO;                             // 2: accumulator ping-pong
   uint64_t* acc_empty = acc_full + 2;                            // 2
   uint64_t* mma_done = acc_empty + 2;                            // every issued MMA finished
@@ -128,18 +177,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr uint32_t kHi = 256, kLo = 384;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < SA; ++i) {
-      mbar_init(&a_full[i], 1);
-      mbar_init(&a_empty[i], 4);
-    }
     for (int i = 0; i < SO; ++i) {
       mbar_init(&b_full[i], 1);
       mbar_init(&o_empty[i], 1);
-      mbar_init(&a_ready[i], 4);
+      mbar_init(&a_ready[i], kConvWarps);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
+      mbar_init(&acc_empty[i], kDrainWarps);
     }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -157,37 +202,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {                                            // ---- TMA producer ----
+    if (lane == 0) {                                            // ---- TMA producer (B) ----
       bool ok = true;
-      int issued_a = 0, issued_b = 0;
+      int issued = 0;
       for (int ks = 0; ks < nk && ok; ++ks) {
-        const int sa = ks % SA, ua = ks / SA, so = ks % SO, uo = ks / SO;
+        const int so = ks % SO, uo = ks / SO;
         const int k0 = k_begin + ks * BK;
-        if (ks >= SA) ok = mbar_wait(&a_empty[sa], (ua - 1) & 1, a.status);
-        if (!ok) break;
-        mbar_expect_tx(&a_full[sa], kStageABytes);
-        if (!TRANS) tma_load_2d(stA + sa * kStageABytes, &tmA, &a_full[sa], k0, m0);
-        else tma_load_2d(stA + sa * kStageABytes, &tmA, &a_full[sa], m0, k0);
-        issued_a = ks + 1;
         if (ks >= SO) ok = mbar_wait(&o_empty[so], (uo - 1) & 1, a.status);
         if (!ok) break;
         mbar_expect_tx(&b_full[so], Q * slice_b_bytes);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
           tma_load_2d(opB + (so * Q + q) * slice_b_bytes, &tmB, &b_full[so], k0, q * a.BNt + n0);
-        issued_b = ks + 1;
+        issued = ks + 1;
       }
       // the last copies into each buffer must have landed before the CTA may exit
-      for (int ks = max(0, issued_a - SA); ks < issued_a; ++ks)
-        mbar_wait(&a_full[ks % SA], (ks / SA) & 1, a.status, false);
-      for (int ks = max(0, issued_b - SO); ks < issued_b; ++ks)
+      for (int ks = max(0, issued - SO); ks < issued; ++ks)
         mbar_wait(&b_full[ks % SO], (ks / SO) & 1, a.status, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {                                            // ---- MMA issuer ----
       const uint32_t idesc = idesc_bf16(BM, BN);
       bool ok = true;
-      int committed = 0;                                        // accumulator groups committed
       for (int g = 0; g < ngroups && ok; ++g) {
         const int b = g & 1;
         if (g >= 2) ok = mbar_wait(&acc_empty[b], ((g >> 1) - 1) & 1, a.status);
@@ -223,32 +259,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (!ok) break;
         mma_commit(&acc_full[b]);
-        committed = g + 1;
       }
-      (void)committed;
       // every MMA this thread issued must have finished before tensor memory is freed
       mma_commit(mma_done);
       mbar_wait(mma_done, 0, a.status, false);
     }
-  } else if (warp < 6) {                                        // ---- A splitters ----
+  } else if (warp < 2 + kConvWarps) {                           // ---- A converters ----
     const int ct = threadIdx.x - 64;
+    float cur[kUnitsPerThread][8], nxt[kUnitsPerThread][8];
+    for (int d = 1; d <= 2 && d < nk; ++d)                      // first tiles towards L2
+      prefetch_tile<TRANS>(a.A, a.lda, a.M, a.K, m0, k_begin + d * BK, ct);
+    if (nk > 0) load_units<TRANS>(a.A, a.lda, a.M, a.K, m0, k_begin, ct, cur);
     bool ok = true;
     for (int ks = 0; ks < nk && ok; ++ks) {
-      const int sa = ks % SA, ua = ks / SA, so = ks % SO, uo = ks / SO;
-      ok = mbar_wait(&a_full[sa], ua & 1, a.status);
-      if (ok && ks >= SO) ok = mbar_wait(&o_empty[so], (uo - 1) & 1, a.status);
+      const int so = ks % SO, uo = ks / SO;
+      if (ks + 3 < nk)                                          // three tiles ahead into L2
+        prefetch_tile<TRANS>(a.A, a.lda, a.M, a.K, m0, k_begin + (ks + 3) * BK, ct);
+      if (ks + 1 < nk)                                          // the next tile in registers
+        load_units<TRANS>(a.A, a.lda, a.M, a.K, m0, k_begin + (ks + 1) * BK, ct, nxt);
+      if (ks >= SO) ok = mbar_wait(&o_empty[so], (uo - 1) & 1, a.status);
       if (!ok) break;
-      split_tile<P, TRANS>(reinterpret_cast<const float*>(stA + sa * kStageABytes),
-                           opA + so * P * kSliceABytes, ct);
+      store_units<P, TRANS>(cur, opA + so * P * kSliceABytes, ct);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&a_empty[sa]);
-        mbar_arrive(&a_ready[so]);
-      }
+      if (lane == 0) mbar_arrive(&a_ready[so]);
+#pragma unroll
+      for (int it = 0; it < kUnitsPerThread; ++it)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) cur[it][e] = nxt[it][e];
     }
   } else {                                                      // ---- accumulator drain ----
     const int quarter = warp & 3;                               // TMEM lanes 32*quarter..+31
+    const int part = (warp - 2 - kConvWarps) >> 2;              // 32-column chunks of this warp
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     bool ok = true;
     int drained = 0;
@@ -257,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       ok = mbar_wait(&acc_full[b], (g >> 1) & 1, a.status);
       if (!ok) break;
       tc_fence_after();
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 32 * part; c0 < BN; c0 += 32 * kDrainParts) {
         uint32_t x[32], hi[32], lo[32];
         tmem_ld32(tmem + lane_base + static_cast<uint32_t>(b * 128 + c0), x);
         if (g == 0) {
@@ -291,7 +333,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int row = m0 + quarter * 32 + lane;
     double* out = a.partial + (static_cast<size_t>(blockIdx.y) * a.M + row) * a.BNt + n0;
     if (ok && drained == ngroups && ngroups > 0) {
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 32 * part; c0 < BN; c0 += 32 * kDrainParts) {
         uint32_t hi[32], lo[32];
         tmem_ld32(tmem + lane_base + kHi + static_cast<uint32_t>(c0), hi);
         tmem_ld32(tmem + lane_base + kLo + static_cast<uint32_t>(c0), lo);
@@ -303,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 static_cast<double>(__uint_as_float(hi[j + 1])) + static_cast<double>(__uint_as_float(lo[j + 1])));
         }
       }
-    } else if (ngroups == 0 && row < a.M) {
+    } else if (ngroups == 0 && row < a.M && part == 0) {
       for (int c = 0; c < BN; ++c) out[c] = 0.0;
     }
   }
@@ -392,33 +434,32 @@ cudaError_t tc_scratch(size_t bytes, void** out) {
   return cudaSuccess;
 }
 
-size_t smem_bytes(int P, int Q, int SA, int SO, int BN) {
-  return static_cast<size_t>(SA) * kStageABytes + static_cast<size_t>(SO) * P * kSliceABytes +
-         static_cast<size_t>(SO) * Q * BN * 128 + 256 + 1024;
+size_t smem_bytes(int P, int Q, int SO, int BN) {
+  return static_cast<size_t>(SO) * (P * kSliceABytes + Q * BN * 128) + 256 + 1024;
 }
 
-template <int P, int Q, bool TRANS, int SA, int SO>
-cudaError_t launch_one(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args,
-                       int splits, cudaStream_t st) {
+template <int P, int Q, bool TRANS, int SO>
+cudaError_t launch_one(const CUtensorMap& mb, const TcArgs& args, int splits, cudaStream_t st) {
   constexpr int DR = (P >= 3) ? 1 : 2;        // reduction steps per accumulator drain
-  auto kernel = sliced_gemm_tc<P, Q, TRANS, SA, SO, DR>;
-  const size_t bytes = smem_bytes(P, Q, SA, SO, args.BN);
+  auto kernel = sliced_gemm_tc<P, Q, TRANS, SO, DR>;
+  const size_t bytes = smem_bytes(P, Q, SO, args.BN);
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
   const dim3 grid(static_cast<unsigned>((args.M + BM - 1) / BM), static_cast<unsigned>(splits),
                   static_cast<unsigned>(args.BNt / args.BN));
-  kernel<<<grid, kTcThreads, bytes, st>>>(ma, mb, args);
+  kernel<<<grid, kTcThreads, bytes, st>>>(mb, args);
   return cudaGetLastError();
 }
 
 template <int P, bool TRANS>
-cudaError_t launch_pq(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args, int splits,
-                      cudaStream_t st) {
-  // stage counts that fit 227 KB: FP32 staging double-buffered, operand stages 2 when they fit
-  if (smem_bytes(P, P, 2, 2, args.BN) <= kMaxNodeSmemBytes)
-    return launch_one<P, P, TRANS, 2, 2>(ma, mb, args, splits, st);
-  return launch_one<P, P, TRANS, 2, 1>(ma, mb, args, splits, st);
+cudaError_t launch_pq(const CUtensorMap& mb, const TcArgs& args, int splits, cudaStream_t st) {
+  // the deepest operand ring that fits 227 KB
+  if (smem_bytes(P, P, 3, args.BN) <= kMaxNodeSmemBytes)
+    return launch_one<P, P, TRANS, 3>(mb, args, splits, st);
+  if (smem_bytes(P, P, 2, args.BN) <= kMaxNodeSmemBytes)
+    return launch_one<P, P, TRANS, 2>(mb, args, splits, st);
+  return launch_one<P, P, TRANS, 1>(mb, args, splits, st);
 }
 
 }  // namespace
@@ -501,26 +542,23 @@ cudaError_t launch_sample_dense_tc(const float* A, int64_t lda, int64_t N, const
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
-  CUtensorMap mAy, mAz, mBy, mBz;
-  const uint64_t arow = static_cast<uint64_t>(lda) * 4;
+  CUtensorMap mBy, mBz;
   const uint64_t brow = static_cast<uint64_t>(ldb) * 2;
   const uint64_t brows = static_cast<uint64_t>(slices) * BNt;
-  if (!make_map(&mAy, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, N, N, arow, BK, BM, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-      !make_map(&mAz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, N, N, arow, BM, BK, CU_TENSOR_MAP_SWIZZLE_NONE) ||
-      !make_map(&mBy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bY, N, brows, brow, BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
+  if (!make_map(&mBy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bY, N, brows, brow, BK, BN, CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&mBz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, bZ, N, brows, brow, BK, BN, CU_TENSOR_MAP_SWIZZLE_128B))
     return cudaErrorInvalidValue;
 
-  TcArgs args{static_cast<int>(N), static_cast<int>(N), BN, BNt, kchunk, partial, status};
+  TcArgs args{A, lda, static_cast<int>(N), static_cast<int>(N), BN, BNt, kchunk, partial, status};
   const unsigned rg = 152u * 8u;
-  e = (slices == 2) ? launch_pq<2, false>(mAy, mBy, args, splits, st)
-                    : launch_pq<3, false>(mAy, mBy, args, splits, st);
+  e = (slices == 2) ? launch_pq<2, false>(mBy, args, splits, st)
+                    : launch_pq<3, false>(mBy, args, splits, st);
   if (e != cudaSuccess) return e;
   reduce_partials<<<rg, 256, 0, st>>>(partial, splits, N, BNt, s, Y);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = (slices == 2) ? launch_pq<2, true>(mAz, mBz, args, splits, st)
-                    : launch_pq<3, true>(mAz, mBz, args, splits, st);
+  e = (slices == 2) ? launch_pq<2, true>(mBz, args, splits, st)
+                    : launch_pq<3, true>(mBz, args, splits, st);
   if (e != cudaSuccess) return e;
   reduce_partials<<<rg, 256, 0, st>>>(partial, splits, N, BNt, s, Z);
   return cudaGetLastError();
