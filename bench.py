@@ -370,19 +370,24 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hbs", choices=["hbs", "reference"])
     ap.add_argument("--N", type=int, default=N_DEF)
-    ap.add_argument("--only", choices=sorted(MODES), default=None,
-                    help="time one precision mode only (default: fp64 headline plus the others)")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated precision modes to time (of " + ", ".join(sorted(MODES))
+                         + "); default: fp64 headline plus the others")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default="logkernel",
-                    choices=["logkernel", "doublelayer", "scaling"],
+                    choices=["logkernel", "doublelayer", "scaling", "batched"],
                     help="logkernel: the timed N = 32768 log-kernel step (default); doublelayer: "
                          "the Section 5.1 boundary-integral operator with r = 30, m = 60, s = 90; "
-                         "scaling: black-box exact-HBS compression for N = 2^16 .. 2^22")
+                         "scaling: black-box exact-HBS compression for N = 2^16 .. 2^22; "
+                         "batched: the 256-operator batch alone")
     ap.add_argument("--max-logN", type=int, default=22)
     args = ap.parse_args()
+    only = [m.strip() for m in args.only.split(",")] if args.only else None
+    if only and any(m not in MODES for m in only):
+        ap.error("--only takes modes from " + ", ".join(sorted(MODES)))
     N, r, s, leaf = args.N, R_DEF, S_DEF, LEAF_DEF
     if args.workload == "doublelayer":
         r, s, leaf = 30, 90, 60
@@ -403,6 +408,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hb.load()
+    if args.workload == "batched":
+        out = run_batched(hb, torch)
+        if rank == 0:
+            print(json.dumps({"workload": "256 exact-HBS operators, batched", "batched": out}),
+                  flush=True)
+        return
     if args.workload == "scaling":
         rows = run_scaling(hb, torch, list(range(16, args.max_logN + 1)))
         if rank == 0:
@@ -423,7 +434,7 @@ def main():
         return float(t.item())
 
     stream = torch.cuda.current_stream()
-    modes = [args.only] if args.only else ["fp64", "oz64", "mixed", "tc64"]
+    modes = only or ["fp64", "oz64", "mixed", "tc64"]
     A = (double_layer_torch if args.workload == "doublelayer" else log_kernel_torch)(N, "cuda")
     A32 = A.float() if any(MODES[m]["a"] == "f32" for m in modes) else None
     Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))

@@ -197,7 +197,8 @@ int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* co
  * Errors: HBS_ERR_ARG, HBS_ERR_CUDA. */
 int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream);
 
-/* Tuning of the sweep launches (Algorithm 2 runs one side and one finish kernel per tree height).
+/* Tuning of the sweep launches (Algorithm 2 runs a side kernel, then the bases, D_tau and merge
+ * kernels, per tree height).
  * hbs_autotune times the side kernel of every height with 1, 2, 3, 4, 6, 8, 12, 16 row slices
  * per node (limited to n/8) on the handle's current inputs -- execute the handle once first --
  * and keeps the fastest; it synchronizes cuda_stream and leaves the factors unchanged.

@@ -229,7 +229,7 @@ void free_handle(hbs_handle* h) {
   delete h;
 }
 
-// The sweep's launches, one side and one finish kernel per height, finest height first.
+// The sweep's launches, one launch_sweep_level per height, finest height first.
 cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
   const bool fp32_finish =
       h->precision == HBS_PREC_MIXED_BF16X3 || h->precision == HBS_PREC_MIXED_BF16X6;

@@ -51,8 +51,8 @@ size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes);   // largest sweep
 constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
 
-// One tree height of Algorithm 2: the side kernel (FP64) then the finish kernel (FP64, or FP32
-// when fp32_finish).
+// One tree height of Algorithm 2: the side kernel (FP64), then the bases, D_tau and merge
+// kernels (FP64, or FP32 when fp32_finish).
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
                                int max_s, bool fp32_finish, int row_splits, int* d_status,
                                cudaStream_t st);

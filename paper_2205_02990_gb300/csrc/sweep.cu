@@ -58,9 +58,19 @@ __device__ __forceinline__ Real warp_sum(Real v) {
   return v;
 }
 
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return ::rsqrt(x); }
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+
 // Reflector of row j of M over columns j..cols-1 (warp 0 only). Leaves v_j in M[j][j..] with
 // the leading 1 stored explicitly, tau_j in tau[j]; with rdiag, also 1/beta_j (the diagonal of
 // L) and a NUMERIC flag if beta_j is zero or not finite.
+// With rho = 1/||x|| (one reciprocal square root) the scalars need one more reciprocal only:
+// beta = -sign(alpha)/rho, 1/beta = -sign(alpha) rho, tau = (beta - alpha)/beta = 1 + |alpha| rho
+// and 1/(alpha - beta) = sign(alpha)/(|alpha| + |beta|). On GB300 a dependent FP64 square root
+// or division costs ~650-700 cycles and a reciprocal or reciprocal square root ~450, and this
+// chain is serial in the factorization.
 template <class Real>
 __device__ void make_reflector(Real* M, int ld, int j, int cols, Real* tau, Real* rdiag,
                                int* status) {
@@ -71,11 +81,17 @@ __device__ void make_reflector(Real* M, int ld, int j, int cols, Real* tau, Real
   for (int k = j + 1 + lane; k < cols; k += 32) ss = fma(row[k], row[k], ss);
   ss = warp_sum(ss);
   const Real alpha = row[j];
-  Real beta = alpha, t = 0, scale = 1;
+  Real beta = alpha, t = 0, scale = 1, inv_beta;
   if (ss != Real(0)) {
-    beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
-    t = (beta - alpha) / beta;
-    scale = Real(1) / (alpha - beta);
+    const Real s2 = fma(alpha, alpha, ss);
+    const Real rho = rsqrt_r(s2);
+    const Real nb = s2 * rho;                          // ||x||
+    beta = -copysign(nb, alpha);
+    inv_beta = -copysign(rho, alpha);
+    t = fma(fabs(alpha), rho, Real(1));
+    scale = copysign(recip(fabs(alpha) + nb), alpha);
+  } else {
+    inv_beta = Real(1) / alpha;                        // H = I; L keeps alpha
   }
   for (int k = j + 1 + lane; k < cols; k += 32) row[k] *= scale;
   __syncwarp();
@@ -83,7 +99,7 @@ __device__ void make_reflector(Real* M, int ld, int j, int cols, Real* tau, Real
     row[j] = 1;
     tau[j] = t;
     if (rdiag != nullptr) {
-      rdiag[j] = Real(1) / beta;
+      rdiag[j] = inv_beta;
       if (!(fabs(beta) > Real(0)) || !isfinite(beta)) atomicOr(status, kStatusNumeric);
     }
   }
@@ -118,6 +134,7 @@ __device__ void lq_factor(Real* M, int ld, int rows, int cols, Real* tau, Real* 
     } else {
       const int remaining = rows - j - 2;                       // rows j+2 .. rows-1
       for (int base = 0; base < remaining; base += kGroups) {
+        if (base + (warp - 1) * (32 / G) >= remaining) break;     // no row for this warp
         const int i = j + 2 + base + gid;
         const bool active = i < rows;
         Real* ri = M + static_cast<size_t>(active ? i : j) * ld;
