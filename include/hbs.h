@@ -198,13 +198,17 @@ int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* co
 int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream);
 
 /* Tuning of the sweep launches (Algorithm 2 runs a side kernel, then the bases, D_tau and merge
- * kernels, per tree height).
- * hbs_autotune times the side kernel of every height with 1, 2, 3, 4, 6, 8, 12, 16 row slices
- * per node (limited to n/8) on the handle's current inputs -- execute the handle once first --
- * and keeps the fastest; it synchronizes cuda_stream and leaves the factors unchanged.
- * hbs_get_tuning returns the number of heights in *heights and copies up to `count` slice counts
- * (0 = automatic) to R (may be NULL); hbs_set_tuning installs saved ones. Errors: HBS_ERR_ARG,
- * HBS_ERR_CUDA. */
+ * kernels, per tree height). The side kernel's shape per height is one integer R: R > 0 splits
+ * each (node, side) into R row slices, each CTA factoring the test block itself; R = -C (C = 2..8)
+ * gives each (node, side) a thread-block cluster of C CTAs that share one factorization (rows
+ * owned round-robin, reflectors published through distributed shared memory); 0 = automatic.
+ * Every shape rounds exactly alike, so the factors do not depend on the tuning.
+ * hbs_autotune times R = 1, 2, 3, 4, 6, 8, 12, 16 and C = 2, 3, 4, 6, 8 (at most n/8, and C only
+ * where the cluster's shared-memory tile fits) on the handle's current inputs -- execute the
+ * handle once first -- and keeps the fastest; it synchronizes cuda_stream and leaves the factors
+ * unchanged. hbs_get_tuning returns the number of heights in *heights and copies up to `count`
+ * values to R (may be NULL); hbs_set_tuning installs saved ones (values below -8 read as -8).
+ * Errors: HBS_ERR_ARG, HBS_ERR_CUDA. */
 int hbs_autotune(hbs_handle* h, void* cuda_stream);
 int hbs_get_tuning(const hbs_handle* h, int32_t* R, int32_t count, int32_t* heights);
 int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count);

@@ -846,10 +846,17 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
     const int ntasks = int(H.tasks.size());
     float best_ms = 1e30f;
     int best = hbs::side_row_splits(ntasks, H.max_n);
-    for (int R : {1, 2, 3, 4, 6, 8, 12, 16}) {
-      if (R > std::max(1, H.max_n / 8)) break;
+    // row slices (each CTA factors the test block) and clusters of C CTAs sharing one
+    // factorization (R = -C)
+    for (int R : {1, 2, 3, 4, 6, 8, 12, 16, -2, -3, -4, -6, -8}) {
+      if (std::abs(R) > std::max(1, H.max_n / 8)) continue;
+      if (R < 0 && !hbs::side_cluster_fits(H.max_n, H.max_s, -R)) continue;
       // one untimed launch, then the mean of three
       cudaError_t e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st);
+      if (R < 0 && e != cudaSuccess && e != cudaErrorLaunchFailure) {
+        cudaGetLastError();                            // a cluster shape the GPU cannot place
+        continue;
+      }
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
       for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st);
@@ -889,7 +896,8 @@ int hbs_get_tuning(const hbs_handle* h, int32_t* R, int32_t count, int32_t* heig
 int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count) {
   if (!h || !R || count < 0) return fail(HBS_ERR_ARG, "hbs_set_tuning: bad arguments");
   h->tuned_R.assign(R, R + count);
-  for (int t = 0; t < count && t < int(h->heights.size()); ++t) h->heights[t].R = std::max(0, R[t]);
+  for (int t = 0; t < count && t < int(h->heights.size()); ++t)
+    h->heights[t].R = std::max(-hbs::kMaxSideCluster, R[t]);
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;

@@ -50,15 +50,19 @@ size_t side_smem_doubles(int n, int s);
 size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes);   // largest sweep-kernel tile
 constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
+constexpr int kMaxSideCluster = 8;      // CTAs sharing one test-block factorization
 
 // One tree height of Algorithm 2: the side kernel (FP64), then the bases, D_tau and merge
 // kernels (FP64, or FP32 when fp32_finish).
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
                                int max_s, bool fp32_finish, int row_splits, int* d_status,
                                cudaStream_t st);
-// The side kernel of one height alone (for tuning its row splits; idempotent).
+// The side kernel of one height alone (for tuning; idempotent). R > 0: R row slices per
+// (node, side), each CTA factoring the test block; R < 0: a cluster of -R CTAs per (node, side)
+// sharing one factorization.
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
-                             int row_splits, int* d_status, cudaStream_t st);
+                             int R, int* d_status, cudaStream_t st);
+bool side_cluster_fits(int n, int s, int C);
 int side_row_splits(int ntasks, int n);
 cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, double* out,
                             cudaStream_t st);

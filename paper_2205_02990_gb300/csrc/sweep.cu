@@ -33,10 +33,14 @@
 // shuffles. The FP64 pipe (2 DFMA per clock per SM on GB300) bounds the side kernel.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "hbs_internal.cuh"
 
 namespace hbs {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int THREADS = 256;
 constexpr int G = 8;                    // lanes per row
@@ -173,15 +177,56 @@ __device__ __forceinline__ void apply_reflector(Real (&y)[NS], const Real* v, Re
   }
 }
 
+// Finishes one transformed sample row y (= s_i Q, lane q holding columns q, q + G, ...): its last
+// r entries to row i of X (n x r, row-major) when X != NULL, and the row of W = S Omega^+ (n x n)
+// from the back substitution W L_1 = (S Q)(:, 0:n), L_1 = lower triangle of F.
+template <int NS>
+__device__ __forceinline__ void store_row(double (&y)[NS], int i, bool active, int n, int s, int r,
+                                          const double* F, int ldF, const double* rdiag,
+                                          double* __restrict__ X, double* __restrict__ W) {
+  const int q = threadIdx.x % G;
+  const int gbase = (threadIdx.x % 32) & ~(G - 1);
+  if (X != nullptr && active) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      if (k >= s - r && k < s) X[static_cast<size_t>(i) * r + (k - (s - r))] = y[t];
+    }
+  }
+  // column-oriented back substitution
+#pragma unroll
+  for (int t = NS - 1; t >= 0; --t) {
+    if (G * t >= n) continue;
+#pragma unroll 1
+    for (int qq = G - 1; qq >= 0; --qq) {
+      const int j = qq + G * t;
+      if (j >= n) continue;
+      const double wj = __shfl_sync(FULL, y[t], gbase + qq) * rdiag[j];
+      if (q == qq) y[t] = wj;
+      const double* Lj = F + static_cast<size_t>(j) * ldF;
+#pragma unroll
+      for (int tt = 0; tt <= t; ++tt) {
+        const int k = q + G * tt;
+        if (k < j) y[tt] = fma(-wj, Lj[k], y[tt]);
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      if (k < n) W[static_cast<size_t>(i) * n + k] = y[t];
+    }
+  }
+}
+
 // Streams rows [row0, row1) of the sample block S (n x s, leading dimension s) through the n
-// reflectors of the factored test block F. Writes the last r entries of each transformed row
-// to X (n x r, row-major) when X != NULL, and the row of W = S Omega^+ (n x n).
+// reflectors of the factored test block F, then finishes them (store_row).
 template <int NS>
 __device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, int row0, int row1,
                             const double* F, int ldF, const double* tau, const double* rdiag,
                             double* __restrict__ X, double* __restrict__ W) {
   const int gid = threadIdx.x / G, q = threadIdx.x % G;
-  const int gbase = (threadIdx.x % 32) & ~(G - 1);
   for (int base = row0; base < row1; base += NGROUPS) {
     const int i = base + gid;
     const bool active = i < row1;
@@ -193,38 +238,7 @@ __device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, i
     }
     for (int j = 0; j < n; ++j)
       apply_reflector<double, NS>(y, F + static_cast<size_t>(j) * ldF, tau[j], j, s, q);
-    if (X != nullptr && active) {
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        const int k = q + G * t;
-        if (k >= s - r && k < s) X[static_cast<size_t>(i) * r + (k - (s - r))] = y[t];
-      }
-    }
-    // W L_1 = (y Q)(0:n): column-oriented back substitution, L_1 = lower triangle of F.
-#pragma unroll
-    for (int t = NS - 1; t >= 0; --t) {
-      if (G * t >= n) continue;
-#pragma unroll 1
-      for (int qq = G - 1; qq >= 0; --qq) {
-        const int j = qq + G * t;
-        if (j >= n) continue;
-        const double wj = __shfl_sync(FULL, y[t], gbase + qq) * rdiag[j];
-        if (q == qq) y[t] = wj;
-        const double* Lj = F + static_cast<size_t>(j) * ldF;
-#pragma unroll
-        for (int tt = 0; tt <= t; ++tt) {
-          const int k = q + G * tt;
-          if (k < j) y[tt] = fma(-wj, Lj[k], y[tt]);
-        }
-      }
-    }
-    if (active) {
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        const int k = q + G * t;
-        if (k < n) W[static_cast<size_t>(i) * n + k] = y[t];
-      }
-    }
+    store_row<NS>(y, i, active, n, s, r, F, ldF, rdiag, X, W);
   }
 }
 
@@ -280,6 +294,130 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
   stream_rows<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, F, ldF, tau, rdiag,
                   side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
+}
+
+// ---- side kernel, cluster form: the C CTAs of a thread-block cluster share one LQ -----------
+//
+// A test block's LQ is a chain of n reflector steps; on one SM it is bounded by that SM's FP64
+// pipe (the row updates) and by the serial reflector generation. Here the C CTAs of a cluster
+// (grid z) hold one (node, side) together. LQ row i lives in CTA i mod C, which applies every
+// reflector to it. When row j+1 is due, warp 0 of its owner applies reflector j to it, generates
+// reflector j+1 and stores the finished row (its part of L and the reflector), tau and 1/beta into
+// the shared memory of every CTA of the cluster; one cluster barrier per step publishes it. Warps
+// 1..7 of every CTA meanwhile apply reflector j to the CTA's rows below j+1 and to its slice of
+// the sample rows (staged in shared memory), so the sample rows ride along with the
+// factorization. Warp 4 shares a scheduler (and its FP64 unit) with warp 0 and takes rows last.
+// After the n-th step every CTA holds the whole factorization and finishes its sample rows.
+__device__ void publish_row(cg::cluster_group& cl, double* F, int ldF, int j, int s, double* tau,
+                            double* rdiag, int C, int c) {
+  const int lane = threadIdx.x % 32;
+  const double* src = F + static_cast<size_t>(j) * ldF;
+  for (int d = 0; d < C; ++d) {
+    if (d == c) continue;
+    double* dst = cl.map_shared_rank(F + static_cast<size_t>(j) * ldF, d);
+    for (int k = lane; k < s; k += 32) dst[k] = src[k];
+    if (lane == 0) {
+      cl.map_shared_rank(tau, d)[j] = tau[j];
+      cl.map_shared_rank(rdiag, d)[j] = rdiag[j];
+    }
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(THREADS, 2)
+    node_side_cluster(const NodeTask* __restrict__ tasks, int* status) {
+  extern __shared__ double smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const NodeTask tk = tasks[blockIdx.x];
+  const int side = blockIdx.y;
+  if (tk.is_root && side == 1) return;                 // the whole cluster leaves together
+  const int C = static_cast<int>(cl.num_blocks());
+  const int c = static_cast<int>(cl.block_rank());
+  const int n = tk.n, r = tk.r, s = tk.s, ldF = s + 1;
+  const int chunk = (n + C - 1) / C;
+  const int row0 = min(n, c * chunk), nrows = min(n, row0 + chunk) - row0;
+  double* F = smem;                                    // n x ldF (every row, once published)
+  double* tau = F + static_cast<size_t>(n) * ldF;      // n
+  double* rdiag = tau + n;                             // n
+  double* Sr = rdiag + n;                              // nrows x ldF: this CTA's sample rows
+  const double* T = side ? tk.Ps : tk.Om;
+  const double* S = side ? tk.Z : tk.Y;
+  const int own = c < n ? (n - 1 - c) / C + 1 : 0;     // rows c, c + C, ...
+  for (int e = threadIdx.x; e < own * s; e += THREADS) {
+    const int i = c + (e / s) * C, k = e % s;
+    F[static_cast<size_t>(i) * ldF + k] = T[static_cast<size_t>(i) * s + k];
+  }
+  for (int e = threadIdx.x; e < nrows * s; e += THREADS) {
+    const int i = e / s, k = e % s;
+    Sr[static_cast<size_t>(i) * ldF + k] = S[static_cast<size_t>(row0 + i) * s + k];
+  }
+  cl.sync();                     // every CTA of the cluster runs before shared memory is shared
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, q = threadIdx.x % G;
+  if (c == 0 && warp == 0) {
+    make_reflector(F, ldF, 0, s, tau, rdiag, status);
+    __syncwarp();
+    publish_row(cl, F, ldF, 0, s, tau, rdiag, C, c);
+  }
+  cl.sync();
+  const int wslot = warp == 4 ? 6 : (warp < 4 ? warp - 1 : warp - 2);   // warps 1..7
+  const int gid = wslot * (32 / G) + lane / G;
+  constexpr int kGroups = (THREADS - 32) / G;
+  for (int j = 0; j < n; ++j) {
+    const double tj = tau[j];
+    const double* v = F + static_cast<size_t>(j) * ldF;
+    if (warp == 0) {
+      if (j + 1 < n && (j + 1) % C == c) {                      // row j+1, then reflector j+1
+        double* ri = F + static_cast<size_t>(j + 1) * ldF;
+        double part = 0;
+        for (int k = j + lane; k < s; k += 32) part = fma(ri[k], v[k], part);
+        const double w = warp_sum(part) * tj;
+        for (int k = j + lane; k < s; k += 32) ri[k] = fma(-w, v[k], ri[k]);
+        __syncwarp();
+        make_reflector(F, ldF, j + 1, s, tau, rdiag, status);
+        __syncwarp();
+        publish_row(cl, F, ldF, j + 1, s, tau, rdiag, C, c);
+      }
+    } else {
+      // items: this CTA's LQ rows i >= j + 2, then its sample rows
+      const int first = j + 2 + ((c - (j + 2)) % C + C) % C;
+      const int nlq = first < n ? (n - 1 - first) / C + 1 : 0;
+      const int items = nlq + nrows;
+      for (int base = 0; base < items; base += kGroups) {
+        if (base + wslot * (32 / G) >= items) break;             // no item for this warp
+        const int it = base + gid;
+        const bool active = it < items;
+        double* ri = !active    ? F + static_cast<size_t>(j) * ldF
+                     : it < nlq ? F + static_cast<size_t>(first + it * C) * ldF
+                                : Sr + static_cast<size_t>(it - nlq) * ldF;
+        // LQ rows split their columns as lq_factor does (lane q: j + q, j + q + G, ...), sample
+        // rows as stream_rows does (lane q: columns = q mod G from the slot holding j), so both
+        // round exactly as the single-CTA kernel
+        const int k0 = (active && it >= nlq) ? (j & ~(G - 1)) + q : j + q;
+        double part = 0;
+        for (int k = k0; k < s; k += G) part = fma(ri[k], k >= j ? v[k] : 0.0, part);
+        const double w = group_sum(part) * tj;
+        if (active)
+          for (int k = k0; k < s; k += G)
+            if (k >= j) ri[k] = fma(-w, v[k], ri[k]);
+      }
+    }
+    cl.sync();
+  }
+  // every reflector and row of L is now local: finish this CTA's sample rows
+  double* X = tk.is_root ? nullptr : (side ? tk.XZ : tk.XY);
+  double* W = tk.is_root ? tk.D : (side ? tk.WZ : tk.WY);
+  const int gidr = threadIdx.x / G;
+  for (int base = 0; base < nrows; base += NGROUPS) {
+    const int i = base + gidr;
+    const bool active = i < nrows;
+    double y[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      y[t] = (active && k < s) ? Sr[static_cast<size_t>(i) * ldF + k] : 0.0;
+    }
+    store_row<NS>(y, row0 + i, active, n, s, tk.is_root ? 0 : r, F, ldF, rdiag, X, W);
+  }
 }
 
 // ---- FP64 finish: bases, D_tau and the parent's blocks in three kernels --------------------
@@ -632,14 +770,52 @@ int side_row_splits(int ntasks, int n) {
   return std::max(1, std::min(want, cap));
 }
 
+size_t side_cluster_smem_doubles(int n, int s, int C) {
+  const size_t chunk = (static_cast<size_t>(n) + C - 1) / C;
+  return side_smem_doubles(n, s) + chunk * (s + 1);
+}
+
+bool side_cluster_fits(int n, int s, int C) {
+  return C >= 2 && C <= kMaxSideCluster && s <= kMaxS &&
+         side_cluster_smem_doubles(n, s, C) * sizeof(double) <= kMaxNodeSmemBytes;
+}
+
+// The side kernel of one height. R > 0: R row slices per (node, side), each CTA factoring the
+// test block itself; R < 0: a cluster of -R CTAs per (node, side) sharing one factorization.
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
-                             int row_splits, int* d_status, cudaStream_t st) {
+                             int R, int* d_status, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
-  const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
-  if (max_s > kMaxS || side_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
-  const int splits = std::max(1, std::min(row_splits, std::max(1, max_n)));
-  const dim3 grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
+  if (max_s > kMaxS) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
+  if (R < 0) {
+    const int C = std::min(-R, kMaxSideCluster);
+    const size_t bytes = side_cluster_smem_doubles(max_n, max_s, C) * sizeof(double);
+    if (bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(C));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = static_cast<unsigned>(C);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    auto side = [&](auto kernel) {
+      e = allow_smem(kernel);
+      if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, kernel, d_tasks, d_status);
+    };
+    if (max_s <= 8 * G) side(node_side_cluster<8>);
+    else if (max_s <= 16 * G) side(node_side_cluster<16>);
+    else side(node_side_cluster<24>);
+    return e;
+  }
+  const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
+  if (side_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
+  const int splits = std::max(1, std::min(R, std::max(1, max_n)));
+  const dim3 grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
   auto side = [&](auto kernel) {
     e = allow_smem(kernel);
     if (e == cudaSuccess) {
@@ -673,20 +849,8 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   if (side_bytes > kMaxNodeSmemBytes || bases_bytes > kMaxNodeSmemBytes ||
       dblk_bytes > kMaxNodeSmemBytes || merge_bytes > kMaxNodeSmemBytes)
     return cudaErrorInvalidValue;
-  const int splits = row_splits > 0 ? std::max(1, std::min(row_splits, std::max(1, max_n)))
-                                    : side_row_splits(ntasks, max_n);
-  const dim3 side_grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
-  cudaError_t e = cudaSuccess;
-  auto side = [&](auto kernel) {
-    e = allow_smem(kernel);
-    if (e == cudaSuccess) {
-      kernel<<<side_grid, THREADS, side_bytes, st>>>(d_tasks, splits, d_status);
-      e = cudaGetLastError();
-    }
-  };
-  if (max_s <= 8 * G) side(node_side<8>);
-  else if (max_s <= 16 * G) side(node_side<16>);
-  else side(node_side<24>);
+  cudaError_t e = launch_side_only(d_tasks, ntasks, max_n, max_s,
+                       row_splits != 0 ? row_splits : side_row_splits(ntasks, max_n), d_status, st);
   if (e != cudaSuccess) return e;
   // bases: one CTA per (node, side); the register slots span the n <= s columns of a basis
   const dim3 bgrid(static_cast<unsigned>(ntasks), 2u);

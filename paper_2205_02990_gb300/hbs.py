@@ -314,7 +314,8 @@ def hbs_load_factors(handle, src):
 
 
 def hbs_autotune(handle):
-    """Time the side kernel's row slicing per tree height on the current inputs; keep the best."""
+    """Time the side kernel's shapes (row slices R > 0, clusters R = -C) per tree height on the
+    current inputs; keep the best."""
     _check(load().hbs_autotune(handle.ptr, _stream()))
 
 

@@ -228,6 +228,20 @@ def test_batch_of_uneven_trees(hb):
     for j, (F, blk) in enumerate(refs):
         worst, where = factor_errors(hb, h, F, blk, range(1, 2 ** (F.L + 1)), item=j)
         assert worst <= 1e-10, (j, worst, where)
+    # the side kernel as clusters sharing one factorization (ragged row ownership, CTAs without
+    # rows where C > n) rounds exactly as the single-CTA form
+    ref = [[hb.hbs_get_node(h, t, item=j) for t in range(1, 2 ** (F.L + 1))]
+           for j, (F, _) in enumerate(refs)]
+    H = len(hb.hbs_get_tuning(h))
+    for tuning in ([-2] * H, [-3] * H, [-8] * H):
+        hb.hbs_set_tuning(h, tuning)
+        hb.hbs_execute(h, probs)
+        hb.hbs_sync_status(h)
+        for j, (F, _) in enumerate(refs):
+            for t, want in zip(range(1, 2 ** (F.L + 1)), ref[j]):
+                got = hb.hbs_get_node(h, t, item=j)
+                for a, b in zip(got, want):
+                    assert (a is None and b is None) or torch.equal(a, b), (tuning, j, t)
 
 
 def test_numeric_status_on_singular_block(hb):
