@@ -308,38 +308,38 @@ __global__ void __launch_bounds__(THREADS, 2)
 // the sample rows (staged in shared memory), so the sample rows ride along with the
 // factorization. Warp 4 shares a scheduler (and its FP64 unit) with warp 0 and takes rows last.
 // After the n-th step every CTA holds the whole factorization and finishes its sample rows.
-__device__ void publish_row(cg::cluster_group& cl, double* F, int ldF, int j, int s, double* tau,
-                            double* rdiag, int C, int c) {
+// Rows of the cluster form carry tau and 1/beta in columns s and s + 1 (the leading dimension is
+// even, so every row starts on 16 bytes): a row goes out as (s + 2) / 2 16-byte stores per CTA.
+__host__ __device__ __forceinline__ int cluster_ld(int s) { return s + 2 + (s & 1); }
+
+__device__ void publish_row(cg::cluster_group& cl, double* F, int ldF, int j, int s, int C, int c) {
   const int lane = threadIdx.x % 32;
-  const double* src = F + static_cast<size_t>(j) * ldF;
+  const double2* src = reinterpret_cast<const double2*>(F + static_cast<size_t>(j) * ldF);
+  const int pairs = (s + 2 + 1) / 2;
   for (int d = 0; d < C; ++d) {
     if (d == c) continue;
-    double* dst = cl.map_shared_rank(F + static_cast<size_t>(j) * ldF, d);
-    for (int k = lane; k < s; k += 32) dst[k] = src[k];
-    if (lane == 0) {
-      cl.map_shared_rank(tau, d)[j] = tau[j];
-      cl.map_shared_rank(rdiag, d)[j] = rdiag[j];
-    }
+    double2* dst = reinterpret_cast<double2*>(cl.map_shared_rank(F + static_cast<size_t>(j) * ldF, d));
+    for (int k = lane; k < pairs; k += 32) dst[k] = src[k];
   }
 }
 
 template <int NS>
 __global__ void __launch_bounds__(THREADS, 2)
     node_side_cluster(const NodeTask* __restrict__ tasks, int* status) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(16) double smem_cl[];
   cg::cluster_group cl = cg::this_cluster();
   const NodeTask tk = tasks[blockIdx.x];
   const int side = blockIdx.y;
   if (tk.is_root && side == 1) return;                 // the whole cluster leaves together
   const int C = static_cast<int>(cl.num_blocks());
   const int c = static_cast<int>(cl.block_rank());
-  const int n = tk.n, r = tk.r, s = tk.s, ldF = s + 1;
+  const int n = tk.n, r = tk.r, s = tk.s, ldF = cluster_ld(s);
   const int chunk = (n + C - 1) / C;
   const int row0 = min(n, c * chunk), nrows = min(n, row0 + chunk) - row0;
-  double* F = smem;                                    // n x ldF (every row, once published)
-  double* tau = F + static_cast<size_t>(n) * ldF;      // n
+  double* F = smem_cl;                                 // n x ldF (every row, once published)
+  double* tau = F + static_cast<size_t>(n) * ldF;      // n (owner's scratch)
   double* rdiag = tau + n;                             // n
-  double* Sr = rdiag + n;                              // nrows x ldF: this CTA's sample rows
+  double* Sr = rdiag + n + (n & 1);                    // nrows x ldF: this CTA's sample rows
   const double* T = side ? tk.Ps : tk.Om;
   const double* S = side ? tk.Z : tk.Y;
   const int own = c < n ? (n - 1 - c) / C + 1 : 0;     // rows c, c + C, ...
@@ -353,18 +353,25 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
   cl.sync();                     // every CTA of the cluster runs before shared memory is shared
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, q = threadIdx.x % G;
-  if (c == 0 && warp == 0) {
-    make_reflector(F, ldF, 0, s, tau, rdiag, status);
+  // reflector j, its tau and 1/beta into row j (columns s, s + 1), then out to the cluster
+  auto finish_reflector = [&](int j) {
+    make_reflector(F, ldF, j, s, tau, rdiag, status);
     __syncwarp();
-    publish_row(cl, F, ldF, 0, s, tau, rdiag, C, c);
-  }
+    if (lane == 0) {
+      F[static_cast<size_t>(j) * ldF + s] = tau[j];
+      F[static_cast<size_t>(j) * ldF + s + 1] = rdiag[j];
+    }
+    __syncwarp();
+    publish_row(cl, F, ldF, j, s, C, c);
+  };
+  if (c == 0 && warp == 0) finish_reflector(0);
   cl.sync();
   const int wslot = warp == 4 ? 6 : (warp < 4 ? warp - 1 : warp - 2);   // warps 1..7
   const int gid = wslot * (32 / G) + lane / G;
   constexpr int kGroups = (THREADS - 32) / G;
   for (int j = 0; j < n; ++j) {
-    const double tj = tau[j];
     const double* v = F + static_cast<size_t>(j) * ldF;
+    const double tj = v[s];
     if (warp == 0) {
       if (j + 1 < n && (j + 1) % C == c) {                      // row j+1, then reflector j+1
         double* ri = F + static_cast<size_t>(j + 1) * ldF;
@@ -373,9 +380,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         const double w = warp_sum(part) * tj;
         for (int k = j + lane; k < s; k += 32) ri[k] = fma(-w, v[k], ri[k]);
         __syncwarp();
-        make_reflector(F, ldF, j + 1, s, tau, rdiag, status);
-        __syncwarp();
-        publish_row(cl, F, ldF, j + 1, s, tau, rdiag, C, c);
+        finish_reflector(j + 1);
       }
     } else {
       // items: this CTA's LQ rows i >= j + 2, then its sample rows
@@ -404,6 +409,8 @@ __global__ void __launch_bounds__(THREADS, 2)
     cl.sync();
   }
   // every reflector and row of L is now local: finish this CTA's sample rows
+  for (int j = threadIdx.x; j < n; j += THREADS) rdiag[j] = F[static_cast<size_t>(j) * ldF + s + 1];
+  __syncthreads();
   double* X = tk.is_root ? nullptr : (side ? tk.XZ : tk.XY);
   double* W = tk.is_root ? tk.D : (side ? tk.WZ : tk.WY);
   const int gidr = threadIdx.x / G;
@@ -772,7 +779,8 @@ int side_row_splits(int ntasks, int n) {
 
 size_t side_cluster_smem_doubles(int n, int s, int C) {
   const size_t chunk = (static_cast<size_t>(n) + C - 1) / C;
-  return side_smem_doubles(n, s) + chunk * (s + 1);
+  const size_t ld = static_cast<size_t>(cluster_ld(s));
+  return static_cast<size_t>(n) * ld + 2 * static_cast<size_t>(n) + (n & 1) + chunk * ld;
 }
 
 bool side_cluster_fits(int n, int s, int C) {
