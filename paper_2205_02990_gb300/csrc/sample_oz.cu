@@ -1,12 +1,12 @@
 // FP64-class sampling Y = A Omega, Z = A^* Psi (Algorithm 2, first block) on the tcgen05 tensor
 // cores by exact products of 8-bit digits: an error-free splitting in the manner of Ozaki,
-// Ogita, Oishi and Rump (Numer. Algorithms 59, 2012), with bfloat16 digits and FP32
+// Ogita, Oishi and Rump (Numer. Algorithms 59, 2012), with FP16 digits and FP32
 // accumulation instead of FP64 slices.
 //
 // Digits. A block of FP64 entries that shares one exponent E (every |x| < 2^(E-1), the largest
 // >= 2^(E-2)) is scaled to the integers X = round(x 2^(8S-E)), |X| <= 2^(8S-1), and each X is
 // written in balanced base 256: X = sum_{i<S} d_i 256^(S-1-i), d_i in [-128, 128]. Then
-// x = sum_i d_i 2^(E-8(i+1)) to within 2^(E-8S-1), and every digit is exact in bfloat16.
+// x = sum_i d_i 2^(E-8(i+1)) to within 2^(E-8S-1), and every digit is exact in FP16.
 // A has one exponent per row and 64-column window (the blocks of Y = A Omega) and one per column
 // and 64-row window (the blocks of Z = A^* Psi, whose reduction runs over the rows of A); the
 // test matrices have one per 64-row window. Digit planes are written once per call by a split
@@ -18,7 +18,7 @@
 // 2^(E_a + E_b - 8d - 16) and sum to an integer of magnitude <= (d + 1) * 64 * 2^14 < 2^23
 // (d < S <= 7), so the tensor core's FP32 accumulator holds every partial sum exactly, in any
 // order and under any rounding of its adder. Pairs with i + j <= S - 1 are formed, S(S+1)/2
-// bf16 tile products per window; each dropped pair weighs at most 2^(2-8S) of max|a| max|b|.
+// FP16 tile products per window; each dropped pair weighs at most 2^(2-8S) of max|a| max|b|.
 //
 // Accumulation. The diagonal d of a window is one accumulator in tensor memory (four of them,
 // several): the MMA thread fills one while eight drain warps scale another by its power of
@@ -37,6 +37,7 @@
 // thread issues tcgen05.mma (M = 128, N = BN, K = 16); warps 2-9 drain. Every wait is bounded
 // and sets the timeout bit of the status word instead of hanging.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -53,7 +54,7 @@ constexpr int kDrainWarps = 8;                  // two per quarter of tensor-mem
 constexpr int kOzThreads = 64 + 32 * kDrainWarps;
 constexpr int OBM = 128;                       // rows of C per CTA (MMA M)
 constexpr int OBK = 64;                        // window: reduction indices per digit tile
-constexpr int kDigitTileA = OBM * OBK * 2;     // one bf16 digit tile of A
+constexpr int kDigitTileA = OBM * OBK * 2;     // one FP16 digit tile of A
 constexpr int kMaxWindowsPerSplit = 32;        // double-float sums span at most 2048 indices
 constexpr int16_t kNoExp = -32768;             // exponent of an all-zero block (the smallest)
 
@@ -87,10 +88,11 @@ __device__ __forceinline__ int64_t scaled_integer(double x, int E) {
     m |= 1ull << 52;
     p = ex - 1075;
   }
+  // m 2^sh < 2^(8S-1): sh <= 2 for normal x, up to 8S - 2 for a block of subnormals
   const int sh = p + 8 * S - E;
   uint64_t X = 0;
   if (E != kNoExp && m != 0 && ex != 0x7ff) {
-    if (sh >= 0) X = m << min(sh, 10);
+    if (sh >= 0) X = m << min(sh, 63);
     else if (sh > -60) X = (m + (1ull << (-sh - 1))) >> (-sh);
   }
   return (u >> 63) ? -static_cast<int64_t>(X) : static_cast<int64_t>(X);
@@ -98,19 +100,7 @@ __device__ __forceinline__ int64_t scaled_integer(double x, int E) {
 
 // The balanced base-256 digits of X (d_i in [-128, 127], the leading one in [-128, 128]) are
 // the bytes of V = X + 128 (256^(S-1) + ... + 1) less 128 each (the leading one: V's bits from
-// 8(S-1) up), with no carries to propagate. This returns the bfloat16 bits of digit i (0: most
-// significant) from the two 32-bit halves of V: the byte is placed under the exponent of 2^23
-// by a byte permute and 2^23 + 128 is subtracted in FP32, exactly.
-template <int S>
-__device__ __forceinline__ uint32_t digit_bits(uint32_t vl, uint32_t vh, int i) {
-  const int k = S - 1 - i;                              // byte position from the bottom
-  uint32_t w;
-  if (k == S - 1) w = 0x4B000000u | (vh >> (8 * (S - 1) - 32));
-  else if (k < 4) w = __byte_perm(vl, 0x4B000000u, 0x7650u | static_cast<uint32_t>(k));
-  else w = __byte_perm(vh, 0x4B000000u, 0x7650u | static_cast<uint32_t>(k - 4));
-  return __float_as_uint(__fsub_rn(__uint_as_float(w), 8388736.0f));   // 2^23 + 128
-}
-
+// 8(S-1) up), with no carries to propagate.
 template <int S>
 __device__ __forceinline__ uint64_t digit_offset() {
   uint64_t c = 0;
@@ -119,28 +109,90 @@ __device__ __forceinline__ uint64_t digit_offset() {
   return c;
 }
 
-__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
-
-// bfloat16 digits of one entry into S planes (plane_stride apart).
+// V for one entry, as two 32-bit words. Normal entries (and zeros) take a branch-free integer
+// path: |x| = m 2^(ex - 1075) with m < 2^53, and X = round(m 2^(2 - t)) with
+// t = E + 1077 - 8S - ex >= 0 (E bounds the block), i.e. ((8m >> t) + 1) >> 1, round half up.
+// Subnormal and non-finite entries take the general form.
 template <int S>
-__device__ __forceinline__ void store_digits(double x, int E, uint16_t* dst, size_t plane_stride) {
-  const uint64_t v = static_cast<uint64_t>(scaled_integer<S>(x, E)) + digit_offset<S>();
-  const uint32_t vl = static_cast<uint32_t>(v), vh = static_cast<uint32_t>(v >> 32);
-#pragma unroll
-  for (int i = 0; i < S; ++i) dst[i * plane_stride] = static_cast<uint16_t>(digit_bits<S>(vl, vh, i) >> 16);
+__device__ __forceinline__ void offset_value(double x, int E, uint32_t& vl, uint32_t& vh) {
+  const uint32_t lx = static_cast<uint32_t>(__double2loint(x));
+  const uint32_t hx = static_cast<uint32_t>(__double2hiint(x));
+  const int ex = static_cast<int>((hx >> 20) & 0x7ffu);
+  uint64_t X;
+  if ((ex == 0 && ((hx & 0xfffffu) | lx) != 0u) || ex == 0x7ff) {
+    const int64_t xi = scaled_integer<S>(x, E);
+    X = static_cast<uint64_t>(xi < 0 ? -xi : xi);
+  } else {
+    const uint32_t mh = (hx & 0xfffffu) | (ex != 0 ? 0x100000u : 0u);
+    const uint64_t u = ((static_cast<uint64_t>(mh) << 32) | lx) << 3;
+    const int t = min(63, max(0, E + 1077 - 8 * S - ex));
+    X = ((u >> t) + 1) >> 1;
+  }
+  const uint64_t sgn = (hx >> 31) ? ~0ull : 0ull;
+  const uint64_t V = digit_offset<S>() + ((X ^ sgn) - sgn);
+  vl = static_cast<uint32_t>(V);
+  vh = static_cast<uint32_t>(V >> 32);
 }
 
-__device__ __forceinline__ uint64_t warp_max64(uint64_t m) {
+// FP16 bits of digit i (0: most significant) of two entries from their V words, packed (the
+// first entry in the low half): the byte (9 bits for the leading digit) goes under the FP16
+// exponent of 1024 (0x6400 | b = 1024 + b) and 1024 + 128 is subtracted, exactly, two at once.
+template <int S>
+__device__ __forceinline__ uint32_t digit_pair_f16(uint32_t l0, uint32_t h0, uint32_t l1,
+                                                   uint32_t h1, int i) {
+  static_assert(S >= 5 && S <= 7, "the leading digit sits in the high word");
+  const int k = S - 1 - i;                              // byte position from the bottom
+  uint32_t w, mask = 0x00ff00ffu;
+  if (k == S - 1) {
+    const uint32_t b = static_cast<uint32_t>(S - 5);    // leading byte in the high word
+    w = __byte_perm(h0, h1, b | ((b + 1) << 4) | ((b + 4) << 8) | ((b + 5) << 12));
+    mask = 0x01ff01ffu;
+  } else if (k < 4) {
+    const uint32_t b = static_cast<uint32_t>(k);
+    w = __byte_perm(l0, l1, b | (b << 4) | ((b + 4) << 8) | ((b + 4) << 12));
+  } else {
+    const uint32_t b = static_cast<uint32_t>(k - 4);
+    w = __byte_perm(h0, h1, b | (b << 4) | ((b + 4) << 8) | ((b + 4) << 12));
+  }
+  w = (w & mask) | 0x64006400u;
+  const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&w),
+                            __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+  return *reinterpret_cast<const uint32_t*>(&d);
+}
+
+// FP16 digits of two neighbouring entries into S planes (plane_stride apart), one 32-bit store
+// per plane.
+template <int S>
+__device__ __forceinline__ void store_digit_pair(double x0, double x1, int E, uint16_t* dst,
+                                                 size_t plane_stride) {
+  uint32_t l0, h0, l1, h1;
+  offset_value<S>(x0, E, l0, h0);
+  offset_value<S>(x1, E, l1, h1);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_xor_sync(0xffffffffu, m, o));
-  return m;
+  for (int i = 0; i < S; ++i)
+    *reinterpret_cast<uint32_t*>(dst + i * plane_stride) = digit_pair_f16<S>(l0, h0, l1, h1, i);
+}
+
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+// The block exponent of 64 entries held two per lane: the largest magnitude's high word is
+// found with one warp reduction (its exponent field, and its leading bit when subnormal); the
+// low words matter only when every high word is zero.
+__device__ __forceinline__ int pair_block_exponent(double x0, double x1, int* status) {
+  const uint32_t a0 = static_cast<uint32_t>(__double2hiint(x0)) & 0x7fffffffu;
+  const uint32_t a1 = static_cast<uint32_t>(__double2hiint(x1)) & 0x7fffffffu;
+  const uint32_t hm = __reduce_max_sync(0xffffffffu, max(a0, a1));
+  if (hm != 0u) return block_exponent(static_cast<uint64_t>(hm) << 32, status);
+  const uint32_t lm = __reduce_max_sync(0xffffffffu, max(static_cast<uint32_t>(__double2loint(x0)),
+                                                          static_cast<uint32_t>(__double2loint(x1))));
+  return block_exponent(static_cast<uint64_t>(lm), status);
 }
 
 // One 64 x 64 block of A: exponents per row (EY) and per column (EZ), digit planes of A (Yd,
 // row-major) and of A^* (Zd). Planes: S x N rows of ldd entries; ldd a multiple of 64.
-// Warp w handles rows (then columns) 8w .. 8w+7; lane l the entries l and l + 32 along them, so
-// that both the row and the column reads of the tile (pitch 65) are free of bank conflicts and
-// every digit store of a warp covers 64 contiguous bytes.
+// Warp w handles rows (then columns) 8w .. 8w+7; lane l the neighbouring entries 2l and 2l + 1
+// along them, so that each digit plane gets one 32-bit store per lane (128 contiguous bytes
+// per warp).
 template <int S>
 __global__ void __launch_bounds__(256)
     oz_split_a(const double* __restrict__ A, int64_t lda, int64_t N, uint16_t* __restrict__ Yd,
@@ -164,24 +216,20 @@ __global__ void __launch_bounds__(256)
 #pragma unroll 1
   for (int rr = 0; rr < 8; ++rr) {                    // rows of A: digits for Y = A Omega
     const int r = warp * 8 + rr;
-    const double x0 = tile[r][lane], x1 = tile[r][lane + 32];
-    const int E = block_exponent(warp_max64(umax64(abs_bits(x0), abs_bits(x1))), status);
+    const double x0 = tile[r][2 * lane], x1 = tile[r][2 * lane + 1];
+    const int E = pair_block_exponent(x0, x1, status);
     if (r0 + r >= N) continue;
     if (lane == 0) EY[(r0 + r) * W + blockIdx.x] = static_cast<int16_t>(E);
-    uint16_t* dst = Yd + (r0 + r) * ldd + c0 + lane;
-    store_digits<S>(x0, E, dst, plane);
-    store_digits<S>(x1, E, dst + 32, plane);
+    store_digit_pair<S>(x0, x1, E, Yd + (r0 + r) * ldd + c0 + 2 * lane, plane);
   }
 #pragma unroll 1
   for (int cc = 0; cc < 8; ++cc) {                    // columns of A: digits for Z = A^* Psi
     const int c = warp * 8 + cc;
-    const double x0 = tile[lane][c], x1 = tile[lane + 32][c];
-    const int E = block_exponent(warp_max64(umax64(abs_bits(x0), abs_bits(x1))), status);
+    const double x0 = tile[2 * lane][c], x1 = tile[2 * lane + 1][c];
+    const int E = pair_block_exponent(x0, x1, status);
     if (c0 + c >= N) continue;
     if (lane == 0) EZ[(c0 + c) * W + blockIdx.y] = static_cast<int16_t>(E);
-    uint16_t* dst = Zd + (c0 + c) * ldd + r0 + lane;
-    store_digits<S>(x0, E, dst, plane);
-    store_digits<S>(x1, E, dst + 32, plane);
+    store_digit_pair<S>(x0, x1, E, Zd + (c0 + c) * ldd + r0 + 2 * lane, plane);
   }
 }
 
@@ -217,11 +265,12 @@ __global__ void __launch_bounds__(256)
     const int c = e >> 6, kk = e & 63;
     const int64_t k = k0 + kk;
     const double x = (c < s && k < N) ? X[k * s + c] : 0.0;
-    const uint64_t v = static_cast<uint64_t>(scaled_integer<S>(x, E)) + digit_offset<S>();
+    uint32_t vl, vh;
+    offset_value<S>(x, E, vl, vh);
 #pragma unroll
     for (int i = 0; i < S; ++i)
-      out[i * plane + static_cast<size_t>(c) * ldd + k] = static_cast<uint16_t>(
-          digit_bits<S>(static_cast<uint32_t>(v), static_cast<uint32_t>(v >> 32), i) >> 16);
+      out[i * plane + static_cast<size_t>(c) * ldd + k] =
+          static_cast<uint16_t>(digit_pair_f16<S>(vl, vh, vl, vh, i));
   }
 }
 
@@ -395,7 +444,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {                                     // ---- MMA issuer ----
-      const uint32_t idesc = idesc_bf16(OBM, BN);
+      const uint32_t idesc = idesc_f16(OBM, BN);
       uint64_t ad[S], bd[S];
 #pragma unroll
       for (int i = 0; i < S; ++i) {

@@ -144,6 +144,18 @@ def test_scale_far_from_one(hb):
         assert rel(np.ldexp(Z, -e), G.T @ Ps) <= 1e-13
 
 
+def test_subnormal_operator(hb):
+    # A ~ 2^-1040: every entry subnormal (~34 significant bits). Its digits need left shifts of
+    # the mantissa by up to ~21 bits; the products land on the subnormal grid (2^-1074), so they
+    # match the exact product to its rounding, 2^-1074 per entry (~1e-10 relative here).
+    N, s = 300, 20
+    A = np.ldexp(gaussian((N, N), 6), -1040)
+    Gs = np.ldexp(A, 1040)                             # exactly A's values, scaled up
+    Om, Ps, Y, Z = sample_tc(hb, A, s, 10)
+    assert rel(np.ldexp(Y, 1040), Gs @ Om) <= 1e-8
+    assert rel(np.ldexp(Z, 1040), Gs.T @ Ps) <= 1e-8
+
+
 def test_non_finite_entry_is_reported(hb):
     N, s = 200, 12
     A = gaussian((N, N), 2)
