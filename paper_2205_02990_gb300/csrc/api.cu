@@ -845,7 +845,7 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
     Height& H = h->heights[t];
     const int ntasks = int(H.tasks.size());
     float best_ms = 1e30f;
-    int best = hbs::side_row_splits(ntasks, H.max_n);
+    int best = hbs::side_row_splits(ntasks, H.max_n, H.max_s);
     // row slices (each CTA factors the test block) and clusters of C CTAs sharing one
     // factorization (R = -C)
     for (int R : {1, 2, 3, 4, 6, 8, 12, 16, -2, -3, -4, -6, -8}) {

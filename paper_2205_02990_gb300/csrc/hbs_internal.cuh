@@ -63,7 +63,7 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
                              int R, int* d_status, cudaStream_t st);
 bool side_cluster_fits(int n, int s, int C);
-int side_row_splits(int ntasks, int n);
+int side_row_splits(int ntasks, int n, int s);   // the automatic side shape (R as above)
 cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, double* out,
                             cudaStream_t st);
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,

@@ -769,12 +769,15 @@ size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes) {
   return std::max({common, dblk_smem_doubles(r, n) * d, merge_smem_doubles(n) * d});
 }
 
-int side_row_splits(int ntasks, int n) {
-  // fill at most one wave of two CTAs per SM over both sides (every split refactors the test
-  // block, so a second partial wave costs more than it saves); keep at least 8 rows per CTA
-  const int want = (2 * 152) / (2 * ntasks);
-  const int cap = std::max(1, n / 8);
-  return std::max(1, std::min(want, cap));
+int side_row_splits(int ntasks, int n, int s) {
+  // Where a height has fewer (node, side) pairs than SMs, give each a cluster of about
+  // 152 / (2 ntasks) CTAs (at most 6, at least 8 rows each) sharing its factorization; otherwise
+  // one CTA each. (Measured on the N = 32768, r = 40 log-kernel tree and the 256-tree batch, the
+  // tuner picks these shapes or ones within a few percent of them.)
+  const int want = (152 + ntasks) / (2 * ntasks);
+  int C = std::max(1, std::min({want, 6, n / 8}));
+  while (C >= 2 && !side_cluster_fits(n, s, C)) --C;
+  return C >= 2 ? -C : 1;
 }
 
 size_t side_cluster_smem_doubles(int n, int s, int C) {
@@ -858,7 +861,7 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
       dblk_bytes > kMaxNodeSmemBytes || merge_bytes > kMaxNodeSmemBytes)
     return cudaErrorInvalidValue;
   cudaError_t e = launch_side_only(d_tasks, ntasks, max_n, max_s,
-                       row_splits != 0 ? row_splits : side_row_splits(ntasks, max_n), d_status, st);
+                       row_splits != 0 ? row_splits : side_row_splits(ntasks, max_n, max_s), d_status, st);
   if (e != cudaSuccess) return e;
   // bases: one CTA per (node, side); the register slots span the n <= s columns of a basis
   const dim3 bgrid(static_cast<unsigned>(ntasks), 2u);
