@@ -309,7 +309,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
 }
 
 template <bool ACC>
-__device__ __forceinline__ void mma_bf16_c(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_f16_c(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                            uint32_t idesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -332,8 +332,8 @@ __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad
     for (int i = 0; i <= D; ++i)
 #pragma unroll
       for (int kk = 0; kk < OBK / 16; ++kk) {
-        if (i == 0 && kk == 0) mma_bf16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
-        else mma_bf16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+        if (i == 0 && kk == 0) mma_f16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+        else mma_f16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
       }
   } else {
     constexpr int G = (S + 1) / 2;
@@ -345,8 +345,8 @@ __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad
         if (t == 1 && i == k) continue;
 #pragma unroll
         for (int kk = 0; kk < OBK / 16; ++kk) {
-          if (k == 0 && t == 0 && kk == 0) mma_bf16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
-          else mma_bf16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+          if (k == 0 && t == 0 && kk == 0) mma_f16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+          else mma_f16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
         }
       }
       mma_commit(&freed[k]);

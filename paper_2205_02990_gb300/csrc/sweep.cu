@@ -366,29 +366,31 @@ __global__ void __launch_bounds__(THREADS, 2)
   };
   if (c == 0 && warp == 0) finish_reflector(0);
   cl.sync();
-  const int wslot = warp == 4 ? 6 : (warp < 4 ? warp - 1 : warp - 2);   // warps 1..7
-  const int gid = wslot * (32 / G) + lane / G;
-  constexpr int kGroups = (THREADS - 32) / G;
+  // in a step where this CTA generates the next reflector, warps 1..7 update (warp 4, which
+  // shares a scheduler and its FP64 unit with warp 0, last); in the other steps all 8 warps do
+  const int wslot = warp == 4 ? 6 : (warp < 4 ? warp - 1 : warp - 2);
   for (int j = 0; j < n; ++j) {
     const double* v = F + static_cast<size_t>(j) * ldF;
     const double tj = v[s];
-    if (warp == 0) {
-      if (j + 1 < n && (j + 1) % C == c) {                      // row j+1, then reflector j+1
-        double* ri = F + static_cast<size_t>(j + 1) * ldF;
-        double part = 0;
-        for (int k = j + lane; k < s; k += 32) part = fma(ri[k], v[k], part);
-        const double w = warp_sum(part) * tj;
-        for (int k = j + lane; k < s; k += 32) ri[k] = fma(-w, v[k], ri[k]);
-        __syncwarp();
-        finish_reflector(j + 1);
-      }
+    const bool chain_step = j + 1 < n && (j + 1) % C == c;
+    if (warp == 0 && chain_step) {                              // row j+1, then reflector j+1
+      double* ri = F + static_cast<size_t>(j + 1) * ldF;
+      double part = 0;
+      for (int k = j + lane; k < s; k += 32) part = fma(ri[k], v[k], part);
+      const double w = warp_sum(part) * tj;
+      for (int k = j + lane; k < s; k += 32) ri[k] = fma(-w, v[k], ri[k]);
+      __syncwarp();
+      finish_reflector(j + 1);
     } else {
       // items: this CTA's LQ rows i >= j + 2, then its sample rows
+      const int slot = chain_step ? wslot : warp;
+      const int ngroups = (chain_step ? THREADS - 32 : THREADS) / G;
+      const int gid = slot * (32 / G) + lane / G;
       const int first = j + 2 + ((c - (j + 2)) % C + C) % C;
       const int nlq = first < n ? (n - 1 - first) / C + 1 : 0;
       const int items = nlq + nrows;
-      for (int base = 0; base < items; base += kGroups) {
-        if (base + wslot * (32 / G) >= items) break;             // no item for this warp
+      for (int base = 0; base < items; base += ngroups) {
+        if (base + slot * (32 / G) >= items) break;              // no item for this warp
         const int it = base + gid;
         const bool active = it < items;
         double* ri = !active    ? F + static_cast<size_t>(j) * ldF
