@@ -36,6 +36,7 @@
 #include <cooperative_groups.h>
 
 #include "hbs_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace hbs {
 namespace {
@@ -302,25 +303,30 @@ __global__ void __launch_bounds__(THREADS, 2)
 // pipe (the row updates) and by the serial reflector generation. Here the C CTAs of a cluster
 // (grid z) hold one (node, side) together. LQ row i lives in CTA i mod C, which applies every
 // reflector to it. When row j+1 is due, warp 0 of its owner applies reflector j to it, generates
-// reflector j+1 and stores the finished row (its part of L and the reflector), tau and 1/beta into
-// the shared memory of every CTA of the cluster; one cluster barrier per step publishes it. Warps
-// 1..7 of every CTA meanwhile apply reflector j to the CTA's rows below j+1 and to its slice of
-// the sample rows (staged in shared memory), so the sample rows ride along with the
-// factorization. Warp 4 shares a scheduler (and its FP64 unit) with warp 0 and takes rows last.
-// After the n-th step every CTA holds the whole factorization and finishes its sample rows.
-// Rows of the cluster form carry tau and 1/beta in columns s and s + 1 (the leading dimension is
-// even, so every row starts on 16 bytes): a row goes out as (s + 2) / 2 16-byte stores per CTA.
+// reflector j+1, writes tau and 1/beta into the row's two spare columns and sends the finished
+// row (its part of L and the reflector) to every other CTA of the cluster with one bulk copy per
+// CTA into distributed shared memory; each CTA has one mbarrier per row, armed for the row's
+// bytes before the loop, and waits on it before the step that uses the row. The other warps
+// meanwhile apply reflector j to the CTA's rows below j+1 and to its slice of the sample rows
+// (staged in shared memory), so the sample rows ride along with the factorization. There is no
+// cluster-wide barrier per step: a row depends only on earlier rows, so the CTAs run ahead or
+// behind each other freely. After the n-th step every CTA holds the whole factorization and
+// finishes its sample rows.
 __host__ __device__ __forceinline__ int cluster_ld(int s) { return s + 2 + (s & 1); }
 
-__device__ void publish_row(cg::cluster_group& cl, double* F, int ldF, int j, int s, int C, int c) {
-  const int lane = threadIdx.x % 32;
-  const double2* src = reinterpret_cast<const double2*>(F + static_cast<size_t>(j) * ldF);
-  const int pairs = (s + 2 + 1) / 2;
-  for (int d = 0; d < C; ++d) {
-    if (d == c) continue;
-    double2* dst = reinterpret_cast<double2*>(cl.map_shared_rank(F + static_cast<size_t>(j) * ldF, d));
-    for (int k = lane; k < pairs; k += 32) dst[k] = src[k];
-  }
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+// Row j (ldF doubles, 16-byte aligned) from this CTA to CTA d's copy of it, completing on d's
+// mbarrier of that row.
+__device__ __forceinline__ void send_row(const double* row, uint64_t* bar, uint32_t bytes, int d) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(cluster_addr(su32(row), d)), "r"(su32(row)), "r"(bytes), "r"(cluster_addr(su32(bar), d))
+      : "memory");
 }
 
 template <int NS>
@@ -334,12 +340,14 @@ __global__ void __launch_bounds__(THREADS, 2)
   const int C = static_cast<int>(cl.num_blocks());
   const int c = static_cast<int>(cl.block_rank());
   const int n = tk.n, r = tk.r, s = tk.s, ldF = cluster_ld(s);
+  const uint32_t row_bytes = static_cast<uint32_t>(ldF) * sizeof(double);
   const int chunk = (n + C - 1) / C;
   const int row0 = min(n, c * chunk), nrows = min(n, row0 + chunk) - row0;
-  double* F = smem_cl;                                 // n x ldF (every row, once published)
+  double* F = smem_cl;                                 // n x ldF (every row, once received)
   double* tau = F + static_cast<size_t>(n) * ldF;      // n (owner's scratch)
   double* rdiag = tau + n;                             // n
-  double* Sr = rdiag + n + (n & 1);                    // nrows x ldF: this CTA's sample rows
+  double* Sr = rdiag + n + (n & 1);                    // chunk x ldF: this CTA's sample rows
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Sr + static_cast<size_t>(chunk) * ldF);   // n
   const double* T = side ? tk.Ps : tk.Om;
   const double* S = side ? tk.Z : tk.Y;
   const int own = c < n ? (n - 1 - c) / C + 1 : 0;     // rows c, c + C, ...
@@ -351,7 +359,13 @@ __global__ void __launch_bounds__(THREADS, 2)
     const int i = e / s, k = e % s;
     Sr[static_cast<size_t>(i) * ldF + k] = S[static_cast<size_t>(row0 + i) * s + k];
   }
-  cl.sync();                     // every CTA of the cluster runs before shared memory is shared
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < n; ++i)
+      if (i % C != c) mbar_expect_tx(&bar[i], row_bytes);     // armed before any copy can start
+  }
+  cl.sync();                     // every CTA runs and has armed its barriers before any copy
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, q = threadIdx.x % G;
   // reflector j, its tau and 1/beta into row j (columns s, s + 1), then out to the cluster
   auto finish_reflector = [&](int j) {
@@ -361,15 +375,19 @@ __global__ void __launch_bounds__(THREADS, 2)
       F[static_cast<size_t>(j) * ldF + s] = tau[j];
       F[static_cast<size_t>(j) * ldF + s + 1] = rdiag[j];
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the copies
     __syncwarp();
-    publish_row(cl, F, ldF, j, s, C, c);
+    if (lane < C && lane != c) send_row(F + static_cast<size_t>(j) * ldF, &bar[j], row_bytes, lane);
   };
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the loaded rows, likewise
+  __syncthreads();
   if (c == 0 && warp == 0) finish_reflector(0);
-  cl.sync();
+  __syncthreads();
   // in a step where this CTA generates the next reflector, warps 1..7 update (warp 4, which
   // shares a scheduler and its FP64 unit with warp 0, last); in the other steps all 8 warps do
   const int wslot = warp == 4 ? 6 : (warp < 4 ? warp - 1 : warp - 2);
   for (int j = 0; j < n; ++j) {
+    if (j % C != c) mbar_wait(&bar[j], 0, status);             // row j from its owner
     const double* v = F + static_cast<size_t>(j) * ldF;
     const double tj = v[s];
     const bool chain_step = j + 1 < n && (j + 1) % C == c;
@@ -408,9 +426,12 @@ __global__ void __launch_bounds__(THREADS, 2)
             if (k >= j) ri[k] = fma(-w, v[k], ri[k]);
       }
     }
-    cl.sync();
+    // rows written here are sent by a bulk copy (the async proxy) in a later step
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
   }
-  // every reflector and row of L is now local: finish this CTA's sample rows
+  // every CTA has received every row: no copy is in flight from or into any CTA of the cluster
+  cl.sync();
   for (int j = threadIdx.x; j < n; j += THREADS) rdiag[j] = F[static_cast<size_t>(j) * ldF + s + 1];
   __syncthreads();
   double* X = tk.is_root ? nullptr : (side ? tk.XZ : tk.XY);
@@ -785,7 +806,8 @@ int side_row_splits(int ntasks, int n, int s) {
 size_t side_cluster_smem_doubles(int n, int s, int C) {
   const size_t chunk = (static_cast<size_t>(n) + C - 1) / C;
   const size_t ld = static_cast<size_t>(cluster_ld(s));
-  return static_cast<size_t>(n) * ld + 2 * static_cast<size_t>(n) + (n & 1) + chunk * ld;
+  // F, tau, 1/beta, the sample rows, one mbarrier per row
+  return static_cast<size_t>(n) * ld + 2 * static_cast<size_t>(n) + (n & 1) + chunk * ld + n;
 }
 
 bool side_cluster_fits(int n, int s, int C) {
