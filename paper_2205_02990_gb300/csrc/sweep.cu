@@ -229,6 +229,7 @@ __device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, i
                             double* __restrict__ X, double* __restrict__ W) {
   const int gid = threadIdx.x / G, q = threadIdx.x % G;
   for (int base = row0; base < row1; base += NGROUPS) {
+    if (base + (threadIdx.x / 32) * (32 / G) >= row1) break;   // no row for this warp
     const int i = base + gid;
     const bool active = i < row1;
     double y[NS];
@@ -250,6 +251,7 @@ __device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int
                            double* __restrict__ B, int ldB) {
   const int gid = threadIdx.x / G, q = threadIdx.x % G;
   for (int base = 0; base < r; base += NGROUPS) {
+    if (base + (threadIdx.x / 32) * (32 / G) >= r) break;      // no column for this warp
     const int c = base + gid;
     const bool active = c < r;
     Real u[NS];
@@ -438,6 +440,7 @@ __global__ void __launch_bounds__(THREADS, 2)
   double* W = tk.is_root ? tk.D : (side ? tk.WZ : tk.WY);
   const int gidr = threadIdx.x / G;
   for (int base = 0; base < nrows; base += NGROUPS) {
+    if (base + warp * (32 / G) >= nrows) break;                // no row for this warp
     const int i = base + gidr;
     const bool active = i < nrows;
     double y[NS];
