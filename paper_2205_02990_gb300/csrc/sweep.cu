@@ -272,8 +272,10 @@ __device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int
 
 // ---- side kernel: LQ of one test block, its sample rows -> W rows and X rows (FP64) ---------
 
-template <int NS>
-__global__ void __launch_bounds__(THREADS, 2)
+// MINB: CTAs per SM the registers are budgeted for (3 where the test block is small enough
+// for three tiles of shared memory per SM, so that more warps hide the FP64 latencies).
+template <int NS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
     node_side(const NodeTask* __restrict__ tasks, int row_splits, int* status) {
   extern __shared__ double smem[];
   const NodeTask tk = tasks[blockIdx.x];
@@ -861,9 +863,11 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
       e = cudaGetLastError();
     }
   };
-  if (max_s <= 8 * G) side(node_side<8>);
-  else if (max_s <= 16 * G) side(node_side<16>);
-  else side(node_side<24>);
+  // three CTAs per SM where three tiles (plus the 1 KB the runtime reserves per CTA) fit
+  const bool three = 3 * (side_bytes + 1024) <= 228 * 1024;
+  if (max_s <= 8 * G) three ? side(node_side<8, 3>) : side(node_side<8, 2>);
+  else if (max_s <= 16 * G) three ? side(node_side<16, 3>) : side(node_side<16, 2>);
+  else three ? side(node_side<24, 3>) : side(node_side<24, 2>);
   return e;
 }
 
