@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 // Real = float in the mixed precisions (the sample block converted once on load; the basis is
 // stored as FP64).
 template <class Real, int NS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 3)   // three CTAs per SM: more warps for the FP64 chains
     node_bases(const NodeTask* __restrict__ tasks, int* status) {
   extern __shared__ __align__(16) unsigned char bsm_bytes[];
   Real* bsm = reinterpret_cast<Real*>(bsm_bytes);
