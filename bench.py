@@ -222,7 +222,7 @@ MODES = {
                  what="A stored FP32; bf16x6 products on tcgen05 tensor cores; FP64 sweep"),
     "oz64": dict(sample=3, sweep=3, a="f64",
                  what="A stored FP64; FP64-class products from 7 exact 8-bit digits per entry "
-                      "(28 bf16 digit-pair products on tcgen05 tensor cores, exact FP32 sums); "
+                      "(28 FP16 digit-pair products on tcgen05 tensor cores, exact FP32 sums); "
                       "FP64 sweep"),
 }
 
@@ -566,7 +566,7 @@ def main():
         peak = BF16_TFLOPS_SUSTAINED
         achieved = 28 * flops_product / res["per_launch"] / 1e12
         roofline = {"kernel": "digit products per FP64 product (oz_split_a/b + oz_gemm + oz_reduce; "
-                              "28 exact bf16 digit-pair products)",
+                              "28 exact FP16 digit-pair products)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
                     "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
@@ -591,7 +591,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "oz64": "f64 (exact bf16 digit products)", "mixed": "bf16x6/f32/f64",
+        "dtype": {"fp64": "f64", "oz64": "f64 (exact FP16 digit products)", "mixed": "bf16x6/f32/f64",
                   "tc64": "bf16x6/f64"}[head], "data": "synthetic",
         "config": {"workload": ("double-layer BIE" if args.workload == "doublelayer" else "log-kernel")
                                + f" N={N} r={r} s={s} leaf={leaf} dense",
