@@ -201,9 +201,10 @@ int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream);
  * kernels, per tree height). The side kernel's shape per height is one integer R: R > 0 splits
  * each (node, side) into R row slices, each CTA factoring the test block itself; R = -C (C = 2..8)
  * gives each (node, side) a thread-block cluster of C CTAs that share one factorization (rows
- * owned round-robin, reflectors published through distributed shared memory); 0 = automatic.
+ * owned round-robin, reflectors published through distributed shared memory; C = 1 is that
+ * form on one CTA, the sample rows updated with the factorization); 0 = automatic.
  * Every shape rounds exactly alike, so the factors do not depend on the tuning.
- * hbs_autotune times R = 1, 2, 3, 4, 6, 8, 12, 16 and C = 2, 3, 4, 6, 8 (at most n/8, and C only
+ * hbs_autotune times R = 1, 2, 3, 4, 6, 8, 12, 16 and C = 1, 2, 3, 4, 6, 8 (at most n/8, and C only
  * where the cluster's shared-memory tile fits) on the handle's current inputs -- execute the
  * handle once first -- and keeps the fastest; it synchronizes cuda_stream and leaves the factors
  * unchanged. hbs_get_tuning returns the number of heights in *heights and copies up to `count`

@@ -848,7 +848,7 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
     int best = hbs::side_row_splits(ntasks, H.max_n, H.max_s);
     // row slices (each CTA factors the test block) and clusters of C CTAs sharing one
     // factorization (R = -C)
-    for (int R : {1, 2, 3, 4, 6, 8, 12, 16, -2, -3, -4, -6, -8}) {
+    for (int R : {1, 2, 3, 4, 6, 8, 12, 16, -1, -2, -3, -4, -6, -8}) {
       if (std::abs(R) > std::max(1, H.max_n / 8)) continue;
       if (R < 0 && !hbs::side_cluster_fits(H.max_n, H.max_s, -R)) continue;
       // one untimed launch, then the mean of three

@@ -816,7 +816,7 @@ size_t side_cluster_smem_doubles(int n, int s, int C) {
 }
 
 bool side_cluster_fits(int n, int s, int C) {
-  return C >= 2 && C <= kMaxSideCluster && s <= kMaxS &&
+  return C >= 1 && C <= kMaxSideCluster && s <= kMaxS &&
          side_cluster_smem_doubles(n, s, C) * sizeof(double) <= kMaxNodeSmemBytes;
 }
 

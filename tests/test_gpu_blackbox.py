@@ -166,7 +166,8 @@ def test_graph_replay_and_tuning_change_nothing(hb):
         assert torch.equal(a, b)
     # row slices (R > 0) and clusters sharing one factorization (R = -C, C rows owners) round
     # exactly alike, whatever the split: C = 3 leaves ragged row ownership at n = 64 and 80
-    for tuning in ([1] * len(R), [-2] * len(R), [-3] * len(R), [-8] * len(R), [-5, 3, -7, 2, -4, -6]):
+    for tuning in ([1] * len(R), [-1] * len(R), [-2] * len(R), [-3] * len(R), [-8] * len(R),
+                   [-5, 3, -7, 2, -4, -6]):
         hb.hbs_set_tuning(h, tuning)
         assert hb.hbs_get_tuning(h) == tuning
         hb.hbs_execute(h, [prob])

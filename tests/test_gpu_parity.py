@@ -233,7 +233,7 @@ def test_batch_of_uneven_trees(hb):
     ref = [[hb.hbs_get_node(h, t, item=j) for t in range(1, 2 ** (F.L + 1))]
            for j, (F, _) in enumerate(refs)]
     H = len(hb.hbs_get_tuning(h))
-    for tuning in ([-2] * H, [-3] * H, [-8] * H):
+    for tuning in ([-1] * H, [-2] * H, [-3] * H, [-8] * H):
         hb.hbs_set_tuning(h, tuning)
         hb.hbs_execute(h, probs)
         hb.hbs_sync_status(h)
