@@ -41,6 +41,8 @@ FP64_PROBE_TFLOPS = 1.056             # measured DFMA throughput on this GB300 (
 GEMM_READ_8192 = 549.46e6             # dram bytes read by one sample_gemm_f64 launch, N = 8192
 GEMM_WRITE_8192 = 42.30e6             # dram bytes written (split-K partials) by that launch
 BF16_TFLOPS_SUSTAINED = 1666.9        # measured dense bf16 peak on this machine's GB300 (sustained)
+HBM_GBS = 6782.1                      # measured copy bandwidth on this machine's GB300
+FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # derived FP64 peak: SMs x DFMA/clk x 2 flop x clock
 
 
 def tree_nodes(N, leaf):
@@ -306,6 +308,45 @@ def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
     return out
 
 
+def run_apply(hb, torch, logN=22, k=45, leaf=64, seed=SEED + 600, reps=5):
+    """Algorithm 1 on its own: Out = A~ X and A~^* X for an exact-HBS operator in telescoping
+    form (N = 2^22, rank 45, leaf 64; the factors loaded into a handle) and X with 1, 16 and 150
+    columns. Bytes: every factor read once, X read once, Out written once (the r-row workspace of
+    the two passes is left out: 2 (2^(L+1) - 2) r c doubles, under 1 % of the factors at c = 1).
+    Flops: 2 c per factor entry. Device-timed (CUDA events), inputs resident."""
+    from hbs_inputs import exact_hbs_packed_torch
+    N = 1 << logN
+    bufs = [torch.empty((N, 3 * k), dtype=torch.float64, device="cuda") for _ in range(4)]
+    gen = hb.hbs_plan([hb.Problem(N, k, 3 * k, leaf, *bufs)])   # the samples are not used
+    del bufs
+    hb.hbs_load_factors(gen, exact_hbs_packed_torch(N, leaf, k, seed, "cuda"))
+    fbytes = hb.hbs_factor_bytes(gen)
+    rows = []
+    for c in (1, 16, 150):
+        X = torch.randn((N, c), dtype=torch.float64, device="cuda")
+        Out = torch.empty_like(X)
+        row = {"ncols": c}
+        for trans in (False, True):
+            hb.hbs_apply(gen, X, Out, trans=trans)        # warm-up (and workspace growth)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                hb.hbs_apply(gen, X, Out, trans=trans)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            nbytes = fbytes + 2 * N * c * 8
+            flops = 2.0 * c * fbytes / 8
+            row["trans" if trans else "plain"] = {
+                "ms": ms, "GB_per_s": nbytes / ms / 1e6, "hbm_frac": nbytes / ms / 1e6 / HBM_GBS,
+                "GFLOP_per_s": flops / ms / 1e6, "fp64_frac": flops / ms / 1e9 / FP64_TFLOPS}
+        rows.append(row)
+        del X, Out
+    gen.free()
+    return {"N": N, "factor_bytes": fbytes, "rows": rows}
+
+
 def run_scaling(hb, torch, logN_list, k=45, r=50, s=150, leaf=64, seed=SEED + 500, reps=2):
     """Linear-complexity check (Section 4.4, Section 5 summary): an exact-HBS operator of block
     rank k = 45 (N = 2^16 .. 2^22, leaf 64) applied as a black box by Algorithm 1 on its loaded
@@ -378,12 +419,14 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default="logkernel",
-                    choices=["logkernel", "doublelayer", "scaling", "batched"],
+                    choices=["logkernel", "doublelayer", "scaling", "batched", "apply"],
                     help="logkernel: the timed N = 32768 log-kernel step (default); doublelayer: "
                          "the Section 5.1 boundary-integral operator with r = 30, m = 60, s = 90; "
                          "scaling: black-box exact-HBS compression for N = 2^16 .. 2^22; "
-                         "batched: the 256-operator batch alone")
-    ap.add_argument("--max-logN", type=int, default=22)
+                         "batched: the 256-operator batch alone; apply: Algorithm 1 on an "
+                         "N = 2^22 exact-HBS operator with 1, 16 and 150 columns")
+    ap.add_argument("--max-logN", type=int, default=22,
+                    help="largest log2 N of the scaling workload; the N of the apply workload")
     args = ap.parse_args()
     only = [m.strip() for m in args.only.split(",")] if args.only else None
     if only and any(m not in MODES for m in only):
@@ -408,6 +451,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     hb.load()
+    if args.workload == "apply":
+        out = run_apply(hb, torch, logN=args.max_logN)
+        if rank == 0:
+            print(json.dumps({"workload": "Algorithm 1, exact-HBS operator, rank 45, leaf 64",
+                              "apply": out}), flush=True)
+        return
     if args.workload == "batched":
         out = run_batched(hb, torch)
         if rank == 0:

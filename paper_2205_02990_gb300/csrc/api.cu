@@ -822,10 +822,15 @@ int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* co
   cudaError_t e = cudaMemcpyAsync(h->d_batch, flat.data(), flat.size() * sizeof(GemmTask),
                                   cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "apply task upload");
+  // one column count for every item: the launch can take the skinny kernel; otherwise each task
+  // carries its own (0)
+  int common = nitems > 0 ? ncols[0] : 0;
+  for (int i = 1; i < nitems; ++i)
+    if (ncols[i] != common) common = 0;
   size_t at = 0;
   for (int cnt : sizes) {
     if (cnt > 0) {
-      e = hbs::launch_gemm_tasks_f64(h->d_batch + at, cnt, 1, st);
+      e = hbs::launch_gemm_tasks_f64(h->d_batch + at, cnt, common, st);
       if (e != cudaSuccess) return cuda_fail(e, "apply kernel");
     }
     at += size_t(cnt);

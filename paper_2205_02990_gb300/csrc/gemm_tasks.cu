@@ -1,12 +1,107 @@
 // Small per-node products of Algorithm 1 (apply): C = op1(A1) B1 [+ op2(A2) B2], one CTA per
-// task, one thread per output element with a K loop. The apply of one level is one launch.
-// At large N the pass is bound by reading X and writing Out once (HBM); factors are small.
+// task. The apply of one level is one launch.
+//
+// Wide right-hand sides (more than kSkinny columns): one thread per output element with a K
+// loop; the products then bound the pass on the FP64 pipe (measured at 90 - 93 % of it for 16
+// and 150 columns).
+//
+// Skinny right-hand sides (1 .. kSkinny columns, a matvec and its neighbours): every factor entry
+// is used by at most kSkinny multiply-adds, so the pass is bound by the FP64 pipe (one DFMA per
+// 8-byte entry is slower on GB300 than reading the entry from HBM), provided the factor, read
+// once from HBM, arrives fast enough: a warp owns 32 rows of C with all their columns and reads
+// the factor coalesced in either storage order (below).
+#include <algorithm>
+
 #include "hbs_internal.cuh"
 
 namespace hbs {
 namespace {
 
 constexpr int THREADS = 256;
+constexpr int kSkinny = 4;          // widest right-hand side of the skinny path
+
+// acc[b] += sum_k op(A)[i][k] B[k][b] over k < K for row i = i0 + lane (< m) of this warp's 32
+// rows. The additions run in k order, as in the wide path, so both give the same bits.
+// op(A) = A^* (entry (i, k) at A[k][i]) is read coalesced along the rows, kUnroll loads ahead of
+// their multiply-adds (the factor is read once from HBM). op(A) = A (entry at A[i][k]) would have
+// each lane walk its own row, one cache line per lane per load (measured: long-scoreboard stalls,
+// the FP64 pipe 55 % busy); instead the warp brings 32 x 32 blocks through its shared-memory tile,
+// one coalesced row segment per load. NC (the columns) is a template parameter, so that no
+// multiply-add is issued for an absent column (predicated ones ran 2.4x slower).
+constexpr int kUnroll = 8;
+template <int NC>
+__device__ __forceinline__ void skinny_term(const double* __restrict__ A, int lda, int t, int K,
+                                            const double* __restrict__ B, int ldb, int m, int i0,
+                                            double* tile, double (&acc)[NC]) {
+  const int lane = threadIdx.x % 32, i = i0 + lane;
+  if (t) {
+    if (i >= m) return;
+    const double* a0 = A + i;
+    int k = 0;
+    for (; k + kUnroll <= K; k += kUnroll) {
+      double a[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) a[u] = a0[static_cast<size_t>(k + u) * lda];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) acc[b] = fma(a[u], B[static_cast<size_t>(k + u) * ldb + b], acc[b]);
+    }
+    for (; k < K; ++k) {
+      const double a = a0[static_cast<size_t>(k) * lda];
+#pragma unroll
+      for (int b = 0; b < NC; ++b) acc[b] = fma(a, B[static_cast<size_t>(k) * ldb + b], acc[b]);
+    }
+    return;
+  }
+  const int rows = min(32, m - i0);
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    const int kw = min(32, K - k0);
+    __syncwarp();
+    if (lane < kw) {
+#pragma unroll 8
+      for (int rr = 0; rr < rows; ++rr)
+        tile[rr * 33 + lane] = A[static_cast<size_t>(i0 + rr) * lda + k0 + lane];
+    }
+    __syncwarp();
+    if (i < m)
+      for (int k = 0; k < kw; ++k) {
+        const double a = tile[lane * 33 + k];
+#pragma unroll
+        for (int b = 0; b < NC; ++b) acc[b] = fma(a, B[static_cast<size_t>(k0 + k) * ldb + b], acc[b]);
+      }
+  }
+}
+
+// A launch whose tasks are all skinny: each warp takes 32 rows of a task (a task of m rows
+// occupies ceil(m / 32) warp slots), slots grid-strided over a few CTAs per SM. (One CTA per
+// task, at ~260,000 tasks per apply, paid the start-up of a CTA, the load of its task and the
+// first memory latency each time.)
+constexpr int kSkinnyThreads = 128;
+template <int NC>
+__global__ void __launch_bounds__(kSkinnyThreads)
+    gemm_tasks_skinny(const GemmTask* __restrict__ tasks, int ntasks, int slots_per_task) {
+  __shared__ double tiles[kSkinnyThreads / 32][32 * 33];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  double* tile = tiles[warp];
+  const long long nslots = static_cast<long long>(ntasks) * slots_per_task;
+  for (long long sl = static_cast<long long>(blockIdx.x) * (kSkinnyThreads / 32) + warp; sl < nslots;
+       sl += static_cast<long long>(gridDim.x) * (kSkinnyThreads / 32)) {
+    const GemmTask t = tasks[sl / slots_per_task];
+    for (int i0 = 32 * static_cast<int>(sl % slots_per_task); i0 < t.m; i0 += 32 * slots_per_task) {
+      double acc[NC];
+#pragma unroll
+      for (int b = 0; b < NC; ++b) acc[b] = 0.0;
+      skinny_term<NC>(t.A1, t.lda1, t.t1, t.k1, t.B1, t.ldb1, t.m, i0, tile, acc);
+      if (t.A2 != nullptr) skinny_term<NC>(t.A2, t.lda2, t.t2, t.k2, t.B2, t.ldb2, t.m, i0, tile, acc);
+      const int i = i0 + lane;
+      if (i < t.m) {
+#pragma unroll
+        for (int b = 0; b < NC; ++b) t.C[static_cast<size_t>(i) * t.ldc + b] = acc[b];
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(THREADS) gemm_tasks_f64(const GemmTask* __restrict__ tasks,
                                                           int ncols) {
@@ -40,6 +135,19 @@ __global__ void __launch_bounds__(THREADS) gemm_tasks_f64(const GemmTask* __rest
 
 cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;
+  if (ncols >= 1 && ncols <= kSkinny) {          // every task has ncols columns
+    // warp slots per task: 2 (rows 0-31 and 32-63 of a task, then 64-95 ... by the same two)
+    const int spt = 2;
+    const long long slots = static_cast<long long>(ntasks) * spt;
+    const int grid = static_cast<int>(std::min<long long>((slots + 3) / 4, 152 * 16));
+    switch (ncols) {
+      case 1: gemm_tasks_skinny<1><<<grid, kSkinnyThreads, 0, st>>>(d_tasks, ntasks, spt); break;
+      case 2: gemm_tasks_skinny<2><<<grid, kSkinnyThreads, 0, st>>>(d_tasks, ntasks, spt); break;
+      case 3: gemm_tasks_skinny<3><<<grid, kSkinnyThreads, 0, st>>>(d_tasks, ntasks, spt); break;
+      default: gemm_tasks_skinny<4><<<grid, kSkinnyThreads, 0, st>>>(d_tasks, ntasks, spt); break;
+    }
+    return cudaGetLastError();
+  }
   gemm_tasks_f64<<<ntasks, THREADS, 0, st>>>(d_tasks, ncols);
   return cudaGetLastError();
 }

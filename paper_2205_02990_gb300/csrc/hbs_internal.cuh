@@ -91,6 +91,8 @@ cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, cons
                                    const double* Ps, int s, double* Y, double* Z, int digits,
                                    cudaStream_t st);
 cudaError_t sample_oz_status(int* host_status, bool clear);
+// ncols: the column count of every task (1 .. 4 takes the grouped skinny kernel), or 0 when each
+// task carries its own.
 cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st);
 
 }  // namespace hbs

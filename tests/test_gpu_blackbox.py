@@ -68,6 +68,47 @@ def test_loaded_factors_apply_matches_blockwise_assembly(hb, N, leaf, k):
     assert rel(Out.cpu().numpy(), A.T) <= 1e-12
 
 
+@pytest.mark.parametrize("N,leaf,k", [(3000, 30, 10), (150, 256, 4)])
+def test_skinny_apply_matches_wide_bitwise(hb, N, leaf, k):
+    # 1 .. 4 right-hand-side columns take the skinny path (one thread per row, factors staged
+    # k-major); wider ones the general path. Both add the products in the same order, so a
+    # column applied alone equals the same column of an 8-column apply bit for bit. N = 150 with
+    # leaf 256 is a single 150 x 150 block, beyond the skinny path's 128 rows: it falls back.
+    g = exact_hbs(N, leaf, k, 7)
+    A = g.dense()
+    h = generator_handle(hb, [g], [leaf])
+    X = torch.as_tensor(np.random.default_rng(N).standard_normal((N, 8)), device="cuda")
+    for trans in (False, True):
+        wide = torch.empty_like(X)
+        hb.hbs_apply(h, X, wide, trans=trans)
+        for c in (1, 3, 4):
+            Xs = X[:, :c].contiguous()
+            out = torch.empty_like(Xs)
+            hb.hbs_apply(h, Xs, out, trans=trans)
+            assert torch.equal(out, wide[:, :c]), (trans, c)
+        ref = (A.T if trans else A) @ X.cpu().numpy()
+        assert rel(wide.cpu().numpy(), ref) <= 1e-12
+
+
+def test_skinny_batched_apply_matches_wide_bitwise(hb):
+    # a batch whose items all have 2 columns takes the grouped skinny kernel; items with unequal
+    # column counts the general one: both equal the wide single-item applies bit for bit
+    gens = [exact_hbs(1200, 24, 8, 11), exact_hbs(700, 20, 6, 12), exact_hbs(90, 128, 5, 13)]
+    h = generator_handle(hb, gens, [24, 20, 128])
+    rng = np.random.default_rng(3)
+    Xw = [torch.as_tensor(rng.standard_normal((g.N, 6)), device="cuda") for g in gens]
+    for trans in (False, True):
+        wide = [torch.empty_like(x) for x in Xw]
+        for j, x in enumerate(Xw):
+            hb.hbs_apply(h, x, wide[j], item=j, trans=trans)
+        for widths in ((2, 2, 2), (1, 3, 2)):
+            Xs = [x[:, :c].contiguous() for x, c in zip(Xw, widths)]
+            Outs = [torch.empty_like(x) for x in Xs]
+            hb.hbs_apply_batch(h, Xs, Outs, trans=trans)
+            for j, (o, c) in enumerate(zip(Outs, widths)):
+                assert torch.equal(o, wide[j][:, :c]), (trans, widths, j)
+
+
 def test_blackbox_callback_pipeline(hb):
     # sampling through a callback that applies the generator handle (Section 1 black box)
     N, k, r, s, leaf, seed = 1000, 6, 9, 27, 18, 21
