@@ -272,8 +272,8 @@ __device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int
 
 // ---- side kernel: LQ of one test block, its sample rows -> W rows and X rows (FP64) ---------
 
-// MINB: CTAs per SM the registers are budgeted for (3 where the test block is small enough
-// for three tiles of shared memory per SM, so that more warps hide the FP64 latencies).
+// MINB: CTAs per SM the registers are budgeted for (3 or 4 where the test block is small enough
+// for that many tiles of shared memory per SM, so that more warps hide the FP64 latencies).
 template <int NS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB)
     node_side(const NodeTask* __restrict__ tasks, int row_splits, int* status) {
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 // Real = float in the mixed precisions (the sample block converted once on load; the basis is
 // stored as FP64).
 template <class Real, int NS>
-__global__ void __launch_bounds__(THREADS, 3)   // three CTAs per SM: more warps for the FP64 chains
+__global__ void __launch_bounds__(THREADS, 4)   // four CTAs per SM: more warps for the FP64 chains
     node_bases(const NodeTask* __restrict__ tasks, int* status) {
   extern __shared__ __align__(16) unsigned char bsm_bytes[];
   Real* bsm = reinterpret_cast<Real*>(bsm_bytes);
@@ -863,11 +863,21 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
       e = cudaGetLastError();
     }
   };
-  // three CTAs per SM where three tiles (plus the 1 KB the runtime reserves per CTA) fit
-  const bool three = 3 * (side_bytes + 1024) <= 228 * 1024;
-  if (max_s <= 8 * G) three ? side(node_side<8, 3>) : side(node_side<8, 2>);
-  else if (max_s <= 16 * G) three ? side(node_side<16, 3>) : side(node_side<16, 2>);
-  else three ? side(node_side<24, 3>) : side(node_side<24, 2>);
+  // four or three CTAs per SM where that many tiles (plus the 1 KB the runtime reserves per
+  // CTA) fit; the register budget follows (64, 80 or 128 per thread, no spills)
+  const int fit = static_cast<int>((228 * 1024) / (side_bytes + 1024));
+  if (max_s <= 8 * G) {
+    if (fit >= 4) side(node_side<8, 4>);
+    else if (fit == 3) side(node_side<8, 3>);
+    else side(node_side<8, 2>);
+  } else if (max_s <= 16 * G) {
+    if (fit >= 4) side(node_side<16, 4>);
+    else if (fit == 3) side(node_side<16, 3>);
+    else side(node_side<16, 2>);
+  } else {
+    if (fit >= 3) side(node_side<24, 3>);
+    else side(node_side<24, 2>);
+  }
   return e;
 }
 
