@@ -233,11 +233,11 @@ def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
     """256 independent exact-HBS operators (N in {2048, 4096, 8192, 16384}, block rank k in
     [8, 32]) compressed with r = k + 5 (Section 4: r = k + p, p = 5 usually suffices; with p = 0
     the method amplifies rounding ~1e7-fold), s = 3r, leaf = largest power of two <= 2r, applied
-    as black boxes (their
-    telescoping factors loaded into a handle, applied by Algorithm 1), sampled by one batched
-    apply per direction, then compressed as one batch: one side and one finish launch per tree
-    height for all 256 trees, replayed from a CUDA graph, row slicing autotuned. Returns timings
-    of the sweep alone (T2) and of drawing + black-box sampling + sweep (T1), FP64 and mixed."""
+    as black boxes (their telescoping factors loaded into a handle, applied by Algorithm 1),
+    sampled by one batched apply per direction, then compressed as one batch: the side, bases,
+    D and merge launches of each tree height cover all 256 trees, replayed from a CUDA graph,
+    side shapes autotuned. Returns timings of the sweep alone (T2) and of drawing + black-box
+    sampling + sweep (T1), FP64 and mixed."""
     import numpy as np
     from hbs_inputs import exact_hbs_packed_torch
     rng = np.random.default_rng(seed)
@@ -501,7 +501,7 @@ def main():
         hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
         hb.hbs_sample_products(Aop, s, Om, Ps, Y, Z, precision=cfg["sample"])
         hb.hbs_execute(h, [prob])
-        hb.hbs_autotune(h)                                 # row slices per height (plan time)
+        hb.hbs_autotune(h)                                 # side shape per height (plan time)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
 
@@ -652,8 +652,12 @@ def main():
         "rel_error": {"opnorm_power20": res.get("rel_error"), "vs": "dense A"},
         "compress_ms": res["elapsed"] / args.steps * 1e3,
         "sweep_gflop": sweep_flops(N, r, s, leaf) / 1e9,
+        # per step: Philox draws + products (FP64: 2 GEMMs + 2 slice sums; bf16x6: 2 right-hand
+        # splits + 2 GEMMs + 2 reductions; digits: 2 test-matrix splits + 1 A split + 2 GEMMs +
+        # 2 reductions), then per tree level the side, bases, D and merge kernels (FP64: D in two
+        # kernels; FP32: one)
         "gpu_launches": args.steps * ({0: 2 + 2 + 2, 2: 2 + 6, 3: 2 + 3 + 4}[MODES[head]["sample"]]
-                                      + 2 * (L + 1)),
+                                      + (4 if MODES[head]["sweep"] in (1, 2) else 5) * (L + 1)),
         "roofline": roofline,
         "clocks": res["clocks"],
         "modes": {m: {"ms_per_step": rr["elapsed"] / args.steps * 1e3,
