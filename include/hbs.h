@@ -149,9 +149,10 @@ typedef struct hbs_handle hbs_handle;   /* opaque: owns the factors and all work
 /* Plan a batch of compressions: validates every problem, builds every tree and allocates the
  * device arena for the factors and workspace. Queues no work. Admissible shapes (Section 4
  * asks for s >= max(r + m, 3r)): with L >= 1, every leaf has between r and s - r rows and
- * s >= 3r; with L = 0 (N <= leaf_max), N <= s. This build also needs s <= 192 and the per-node
- * shared-memory tiles to fit: n (s + 1) + 2n <= 29056 and (r + n)(n + 1) + r n + r <= 29056
- * doubles for every node of n rows.
+ * s >= 3r; with L = 0 (N <= leaf_max), N <= s. This build also needs s <= 192 and, for every
+ * node of n rows, the sweep kernels' shared-memory tiles within 227 KB: the test block,
+ * n (s + 1) + 2n doubles; the basis tile, r (n + 1) + n (r + 1) + 10 r doubles (floats in the
+ * mixed precisions); in the mixed precisions the D tile, r (n + 1) + 3 n r + 3 n^2 + n floats.
  * Sweep precision: HBS_PREC_FP64 keeps every step in FP64; the mixed precisions keep the LQ of
  * each test block (nullspace and pseudo-inverse) and the sample rows pushed through it in FP64
  * and compute the bases, D_tau and the parent blocks in FP32 (factors stored in FP64).

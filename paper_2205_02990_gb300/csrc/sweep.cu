@@ -245,29 +245,46 @@ __device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, i
 }
 
 // Basis B (n x r, leading dimension ldB, FP64 storage) = first r columns of H_0 ... H_{r-1},
-// the reflectors of the LQ of XT (r x n) -- i.e. col(X, r) for X = XT^*.
-template <class Real, int NS>
-__device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int n,
-                           double* __restrict__ B, int ldB) {
-  const int gid = threadIdx.x / G, q = threadIdx.x % G;
-  for (int base = 0; base < r; base += NGROUPS) {
-    if (base + (threadIdx.x / 32) * (32 / G) >= r) break;      // no column for this warp
-    const int c = base + gid;
-    const bool active = c < r;
-    Real u[NS];
-#pragma unroll
-    for (int t = 0; t < NS; ++t) u[t] = (q + G * t == c) ? Real(1) : Real(0);
-    const int jmax = min(r, base + NGROUPS) - 1;
-    for (int j = jmax; j >= 0; --j)
-      apply_reflector<Real, NS>(u, XT + static_cast<size_t>(j) * ldX, tau2[j], j, n, q);
-    if (active) {
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        const int k = q + G * t;
-        if (k < n) B[static_cast<size_t>(k) * ldB + c] = static_cast<double>(u[t]);
-      }
+// the reflectors of the LQ of XT (r x n) -- i.e. col(X, r) for X = XT^*. Backward accumulation
+// on an n x r tile W in shared memory: W = [I_r; 0], then W <- H_j W for j = r-1 .. 0. H_j acts
+// on rows j.. only, where the columns c < j of W are still zero, so step j touches the block of
+// rows j.. and columns j.. . Lanes run over columns and warps over rows: the dot products
+// v_j^* W are summed per warp, the eight partial sums added by one thread per column (no
+// shuffles, no integer divisions). scratch: 8 r + r Reals.
+template <class Real>
+__device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int n, Real* W,
+                           Real* scratch, double* __restrict__ B, int ldB) {
+  constexpr int kWarps = THREADS / 32;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int ldW = r + 1;
+  Real* part = scratch;                                // kWarps x r
+  Real* wsum = scratch + kWarps * r;                   // r
+  for (int i = warp; i < n; i += kWarps)
+    for (int c = lane; c < r; c += 32) W[i * ldW + c] = (i == c) ? Real(1) : Real(0);
+  __syncthreads();
+  for (int j = r - 1; j >= 0; --j) {
+    const Real* v = XT + static_cast<size_t>(j) * ldX;  // v[j] = 1, v[i > j] the tail
+    for (int c = j + lane; c < r; c += 32) {
+      Real acc = 0;
+      for (int i = j + warp; i < n; i += kWarps) acc = fma(v[i], W[i * ldW + c], acc);
+      part[warp * r + c] = acc;
     }
+    __syncthreads();
+    if (threadIdx.x >= j && threadIdx.x < r) {
+      Real w = 0;
+#pragma unroll
+      for (int ww = 0; ww < kWarps; ++ww) w += part[ww * r + threadIdx.x];
+      wsum[threadIdx.x] = w * tau2[j];
+    }
+    __syncthreads();
+    for (int c = j + lane; c < r; c += 32) {
+      const Real w = wsum[c];
+      for (int i = j + warp; i < n; i += kWarps) W[i * ldW + c] = fma(-v[i], w, W[i * ldW + c]);
+    }
+    __syncthreads();
   }
+  for (int i = warp; i < n; i += kWarps)
+    for (int c = lane; c < r; c += 32) B[static_cast<size_t>(i) * ldB + c] = static_cast<double>(W[i * ldW + c]);
 }
 
 // ---- side kernel: LQ of one test block, its sample rows -> W rows and X rows (FP64) ---------
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 // columns formed explicitly.
 // Real = float in the mixed precisions (the sample block converted once on load; the basis is
 // stored as FP64).
-template <class Real, int NS>
+template <class Real>
 __global__ void __launch_bounds__(THREADS, 4)   // four CTAs per SM: more warps for the FP64 chains
     node_bases(const NodeTask* __restrict__ tasks, int* status) {
   extern __shared__ __align__(16) unsigned char bsm_bytes[];
@@ -480,12 +497,14 @@ __global__ void __launch_bounds__(THREADS, 4)   // four CTAs per SM: more warps 
   const int ldX = n + 1;
   Real* XT = bsm;                                      // r x ldX: (Y P)^* or (Z Q)^*
   Real* tau2 = XT + static_cast<size_t>(r) * ldX;      // r
+  Real* W = tau2 + r;                                  // n x (r + 1): the basis being formed
+  Real* scratch = W + static_cast<size_t>(n) * (r + 1);  // 9 r
   const double* X = blockIdx.y ? tk.XZ : tk.XY;
   for (int e = threadIdx.x; e < n * r; e += THREADS)
     XT[(e % r) * ldX + e / r] = static_cast<Real>(X[e]);
   __syncthreads();
   lq_factor<Real>(XT, ldX, r, n, tau2, nullptr, status);
-  form_basis<Real, NS>(XT, ldX, tau2, r, n, blockIdx.y ? tk.V : tk.U, r);
+  form_basis<Real>(XT, ldX, tau2, r, n, W, scratch, blockIdx.y ? tk.V : tk.U, r);
 }
 
 // Columns [j0, j0 + nb) of P = U^* WY and Q = U^* WZ^*, into the spent XZ and XY (r x n).
@@ -768,7 +787,9 @@ size_t side_smem_doubles(int n, int s) {
 
 
 size_t merge_smem_doubles(int n) { return 2 * static_cast<size_t>(n) * kMergeCols; }
-size_t bases_smem_doubles(int n, int r) { return static_cast<size_t>(r) * (n + 1) + r; }
+size_t bases_smem_doubles(int n, int r) {   // in units of the kernel's Real
+  return static_cast<size_t>(r) * (n + 1) + r + static_cast<size_t>(n) * (r + 1) + 9 * static_cast<size_t>(r);
+}
 size_t dblk_smem_doubles(int r, int nb) {
   return static_cast<size_t>(r) * r + static_cast<size_t>(r) * nb;
 }
@@ -914,13 +935,9 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
     }
   };
   if (fp32_finish) {
-    if (max_n <= 8 * G) bases(node_bases<float, 8>);
-    else if (max_n <= 16 * G) bases(node_bases<float, 16>);
-    else bases(node_bases<float, 24>);
+    bases(node_bases<float>);
   } else {
-    if (max_n <= 8 * G) bases(node_bases<double, 8>);
-    else if (max_n <= 16 * G) bases(node_bases<double, 16>);
-    else bases(node_bases<double, 24>);
+    bases(node_bases<double>);
   }
   if (e != cudaSuccess) return e;
   const dim3 merge_grid(static_cast<unsigned>(ntasks),
