@@ -25,8 +25,8 @@ constexpr int kSkinny = 4;          // widest right-hand side of the skinny path
 // op(A) = A^* (entry (i, k) at A[k][i]) is read coalesced along the rows, kUnroll loads ahead of
 // their multiply-adds (the factor is read once from HBM). op(A) = A (entry at A[i][k]) would have
 // each lane walk its own row, one cache line per lane per load (measured: long-scoreboard stalls,
-// the FP64 pipe 55 % busy); instead the warp brings 32 x 32 blocks through its shared-memory tile,
-// one coalesced row segment per load. NC (the columns) is a template parameter, so that no
+// the FP64 pipe 55 % busy); instead the warp brings 32 x 32 blocks through two shared-memory
+// tiles, one coalesced row segment per copy, the next block in flight while one is used. NC (the columns) is a template parameter, so that no
 // multiply-add is issued for an absent column (predicated ones ran 2.4x slower).
 constexpr int kUnroll = 8;
 template <int NC>
@@ -54,22 +54,39 @@ __device__ __forceinline__ void skinny_term(const double* __restrict__ A, int ld
     }
     return;
   }
+  // two tiles: the next 32 x 32 block streams in by asynchronous copies while this one is used
   const int rows = min(32, m - i0);
-  for (int k0 = 0; k0 < K; k0 += 32) {
+  auto fetch = [&](int k0, double* tl) {
     const int kw = min(32, K - k0);
-    __syncwarp();
     if (lane < kw) {
 #pragma unroll 8
       for (int rr = 0; rr < rows; ++rr)
-        tile[rr * 33 + lane] = A[static_cast<size_t>(i0 + rr) * lda + k0 + lane];
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(tl + rr * 33 + lane))),
+                     "l"(A + static_cast<size_t>(i0 + rr) * lda + k0 + lane)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  __syncwarp();
+  fetch(0, tile);
+  for (int k0 = 0, c = 0; k0 < K; k0 += 32, ++c) {
+    double* cur = tile + (c & 1) * 32 * 33;
+    if (k0 + 32 < K) {
+      fetch(k0 + 32, tile + ((c + 1) & 1) * 32 * 33);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncwarp();
+    const int kw = min(32, K - k0);
     if (i < m)
       for (int k = 0; k < kw; ++k) {
-        const double a = tile[lane * 33 + k];
+        const double a = cur[lane * 33 + k];
 #pragma unroll
         for (int b = 0; b < NC; ++b) acc[b] = fma(a, B[static_cast<size_t>(k0 + k) * ldb + b], acc[b]);
       }
+    __syncwarp();                            // before the tile is refilled
   }
 }
 
@@ -77,11 +94,11 @@ __device__ __forceinline__ void skinny_term(const double* __restrict__ A, int ld
 // occupies ceil(m / 32) warp slots), slots grid-strided over a few CTAs per SM. (One CTA per
 // task, at ~260,000 tasks per apply, paid the start-up of a CTA, the load of its task and the
 // first memory latency each time.)
-constexpr int kSkinnyThreads = 128;
+constexpr int kSkinnyThreads = 64;      // two warps: 2 x 2 tiles of 32 x 33 doubles
 template <int NC>
 __global__ void __launch_bounds__(kSkinnyThreads)
     gemm_tasks_skinny(const GemmTask* __restrict__ tasks, int ntasks, int slots_per_task) {
-  __shared__ double tiles[kSkinnyThreads / 32][32 * 33];
+  __shared__ double tiles[kSkinnyThreads / 32][2 * 32 * 33];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   double* tile = tiles[warp];
   const long long nslots = static_cast<long long>(ntasks) * slots_per_task;
@@ -139,7 +156,7 @@ cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols
     // warp slots per task: 2 (rows 0-31 and 32-63 of a task, then 64-95 ... by the same two)
     const int spt = 2;
     const long long slots = static_cast<long long>(ntasks) * spt;
-    const int grid = static_cast<int>(std::min<long long>((slots + 3) / 4, 152 * 16));
+    const int grid = static_cast<int>(std::min<long long>((slots + 1) / 2, 152 * 32));
     switch (ncols) {
       case 1: gemm_tasks_skinny<1><<<grid, kSkinnyThreads, 0, st>>>(d_tasks, ntasks, spt); break;
       case 2: gemm_tasks_skinny<2><<<grid, kSkinnyThreads, 0, st>>>(d_tasks, ntasks, spt); break;

@@ -90,6 +90,30 @@ def test_skinny_apply_matches_wide_bitwise(hb, N, leaf, k):
         assert rel(wide.cpu().numpy(), ref) <= 1e-12
 
 
+def test_repeated_apply_reuses_work_list_correctly(hb):
+    # repeated calls with the same buffers reuse the uploaded work list: new contents of X, new
+    # factors loaded into the handle, another direction and another stream must all show
+    N, leaf, k = 900, 20, 6
+    g1, g2 = exact_hbs(N, leaf, k, 21), exact_hbs(N, leaf, k, 22)
+    h = generator_handle(hb, [g1], [leaf])
+    X = torch.empty((N, 2), dtype=torch.float64, device="cuda")
+    Out = torch.empty_like(X)
+    rng = np.random.default_rng(5)
+    for g, trans in ((g1, False), (g1, False), (g1, True), (g2, False), (g2, True)):
+        if g is g2:
+            hb.hbs_load_factors(h, torch.as_tensor(pack_telescoping(g2), device="cuda"))
+        X.copy_(torch.as_tensor(rng.standard_normal((N, 2))))
+        hb.hbs_apply(h, X, Out, trans=trans)
+        A = g.dense()
+        ref = (A.T if trans else A) @ X.cpu().numpy()
+        assert rel(Out.cpu().numpy(), ref) <= 1e-12
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        hb.hbs_apply(h, X, Out)
+    side.synchronize()
+    assert rel(Out.cpu().numpy(), g2.dense() @ X.cpu().numpy()) <= 1e-12
+
+
 def test_skinny_batched_apply_matches_wide_bitwise(hb):
     # a batch whose items all have 2 columns takes the grouped skinny kernel; items with unequal
     # column counts the general one: both equal the wide single-item applies bit for bit
