@@ -118,6 +118,11 @@ struct hbs_handle {
     }
   } apply_key;
   std::vector<int> apply_sizes;                        // tasks per pass of that list
+  // likewise for hbs_apply_batch and d_batch: direction, stream, workspace, then per item
+  // (X, Out, columns)
+  std::vector<uintptr_t> batch_key;
+  std::vector<int> batch_sizes;
+  int batch_ncols = 0;
   std::vector<int> tuned_R;   // per height, kept across task rebuilds
   // the sweep's launches captured once per set of inputs and replayed
   bool use_graph = true;
@@ -772,6 +777,31 @@ int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* co
     need += 2 * ((size_t(2) << it.L) - 2) * size_t(it.r) * size_t(ncols[i]);
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<uintptr_t> key;
+  key.reserve(3 + 3 * size_t(nitems));
+  key.push_back(uintptr_t(trans));
+  key.push_back(reinterpret_cast<uintptr_t>(st));
+  for (int i = 0; i < nitems; ++i) {
+    key.push_back(reinterpret_cast<uintptr_t>(X[i]));
+    key.push_back(reinterpret_cast<uintptr_t>(Out[i]));
+    key.push_back(uintptr_t(ncols[i]));
+  }
+  if (need <= h->batch_ws_doubles) {
+    key.push_back(reinterpret_cast<uintptr_t>(h->batch_ws));
+    if (key == h->batch_key) {                         // the uploaded list still applies
+      size_t at = 0;
+      for (int cnt : h->batch_sizes) {
+        if (cnt > 0) {
+          cudaError_t e = hbs::launch_gemm_tasks_f64(h->d_batch + at, cnt, h->batch_ncols, st);
+          if (e != cudaSuccess) return cuda_fail(e, "apply kernel");
+        }
+        at += size_t(cnt);
+      }
+      return ok();
+    }
+    key.pop_back();
+  }
+  h->batch_key.clear();
   if (need > h->batch_ws_doubles) {
     cudaFree(h->batch_ws);
     h->batch_ws = nullptr;
@@ -865,6 +895,10 @@ int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* co
     }
     at += size_t(cnt);
   }
+  key.push_back(reinterpret_cast<uintptr_t>(h->batch_ws));
+  h->batch_key = std::move(key);
+  h->batch_sizes = sizes;
+  h->batch_ncols = common;
   return ok();
 }
 

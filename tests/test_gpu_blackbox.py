@@ -112,6 +112,18 @@ def test_repeated_apply_reuses_work_list_correctly(hb):
         hb.hbs_apply(h, X, Out)
     side.synchronize()
     assert rel(Out.cpu().numpy(), g2.dense() @ X.cpu().numpy()) <= 1e-12
+    # the batched apply reuses its list the same way
+    g3 = exact_hbs(500, 16, 5, 23)
+    hbb = generator_handle(hb, [g1, g3], [leaf, 16])
+    Xs = [torch.empty((g.N, 3), dtype=torch.float64, device="cuda") for g in (g1, g3)]
+    Outs = [torch.empty_like(x) for x in Xs]
+    for trans in (False, False, True, True):
+        for x in Xs:
+            x.copy_(torch.as_tensor(rng.standard_normal(tuple(x.shape))))
+        hb.hbs_apply_batch(hbb, Xs, Outs, trans=trans)
+        for g, x, o in zip((g1, g3), Xs, Outs):
+            A = g.dense()
+            assert rel(o.cpu().numpy(), (A.T if trans else A) @ x.cpu().numpy()) <= 1e-12
 
 
 def test_skinny_batched_apply_matches_wide_bitwise(hb):
