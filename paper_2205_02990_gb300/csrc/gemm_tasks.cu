@@ -1,9 +1,9 @@
-// Small per-node products of Algorithm 1 (apply): C = op1(A1) B1 [+ op2(A2) B2], one CTA per
-// task. The apply of one level is one launch.
+// Small per-node products of Algorithm 1 (apply): C = op1(A1) B1 [+ op2(A2) B2]. The apply of
+// one level is one launch.
 //
-// Wide right-hand sides (more than kSkinny columns): one thread per output element with a K
-// loop; the products then bound the pass on the FP64 pipe (measured at 90 - 93 % of it for 16
-// and 150 columns).
+// Wide right-hand sides (more than kSkinny columns): one CTA per task, one thread per output
+// element with a K loop; the products then bound the pass on the FP64 pipe (measured at 93 - 94 %
+// of it for 16 and 150 columns).
 //
 // Skinny right-hand sides (1 .. kSkinny columns, a matvec and its neighbours): every factor entry
 // is used by at most kSkinny multiply-adds, so the pass is bound by the FP64 pipe (one DFMA per
@@ -26,8 +26,9 @@ constexpr int kSkinny = 4;          // widest right-hand side of the skinny path
 // their multiply-adds (the factor is read once from HBM). op(A) = A (entry at A[i][k]) would have
 // each lane walk its own row, one cache line per lane per load (measured: long-scoreboard stalls,
 // the FP64 pipe 55 % busy); instead the warp brings 32 x 32 blocks through two shared-memory
-// tiles, one coalesced row segment per copy, the next block in flight while one is used. NC (the columns) is a template parameter, so that no
-// multiply-add is issued for an absent column (predicated ones ran 2.4x slower).
+// tiles, one coalesced row segment per copy, the next block in flight while one is used. NC (the
+// columns) is a template parameter, so that no multiply-add is issued for an absent column
+// (predicated ones ran 2.4x slower).
 constexpr int kUnroll = 8;
 template <int NC>
 __device__ __forceinline__ void skinny_term(const double* __restrict__ A, int lda, int t, int K,
