@@ -1,4 +1,4 @@
-// Per-level sweep of Algorithm 2: two kernels per tree level.
+// Per-level sweep of Algorithm 2: the kernels of one tree level.
 //
 // For a node tau with blocks Omega_tau, Psi_tau, Y_tau, Z_tau (n x s) the sweep computes
 //   P = null(Omega_tau, r), U = col(Y_tau P, r)              (Section 4.1, Eq. u_tau_formula)
@@ -8,29 +8,28 @@
 //   V^* Omega_tau, U^* Psi_tau, U^* (Y_tau - D Omega_tau), V^* (Z_tau - D^* Psi_tau).
 // At the root only D = Y Omega^+ (Section 4.3).
 //
-// Side kernel (FP64 in every precision: it holds the nullspace and the pseudo-inverse). One
-// CTA per (node, side, slice of rows); side 0 works on Omega_tau and Y_tau, side 1 on Psi_tau
-// and Z_tau. One Householder LQ of the test block, Omega_tau = L Q^* (the QR of Omega_tau^* of
-// Section 2.4, Q square), serves both `null` and the pseudo-inverse: the last r columns of Q
-// are null(Omega_tau, r), and Omega_tau = L_1 Q_1^* with L_1 the leading n x n lower triangle
-// gives Omega^+ = Q_1 L_1^{-1}. Each sample row y is pushed once through the n reflectors
-// (y Q = y H_0 ... H_{n-1}): its last r entries are the row of Y_tau P, its first n entries,
-// solved against L_1, the row of Y_tau Omega^+. Neither P nor Q is formed. Where a level has
-// few nodes, the rows are split across several CTAs (each refactors the small test block), so
-// that the upper levels of the tree still fill the GPU.
+// Side kernel (FP64 in every precision: it holds the nullspace and the pseudo-inverse); side 0
+// works on Omega_tau and Y_tau, side 1 on Psi_tau and Z_tau. One Householder LQ of the test
+// block, Omega_tau = L Q^* (the QR of Omega_tau^* of Section 2.4, Q square), serves both `null`
+// and the pseudo-inverse: the last r columns of Q are null(Omega_tau, r), and
+// Omega_tau = L_1 Q_1^* with L_1 the leading n x n lower triangle gives Omega^+ = Q_1 L_1^{-1}.
+// Each sample row y is pushed once through the n reflectors (y Q = y H_0 ... H_{n-1}): its last
+// r entries are the row of Y_tau P, its first n entries, solved against L_1, the row of
+// Y_tau Omega^+. Neither P nor Q is formed. Two forms, which round alike: node_side (one CTA per
+// (node, side), or per row slice, each slice refactoring the block) and node_side_cluster (a
+// thread-block cluster shares one factorization, below), for the levels with few nodes.
 //
-// Finish kernel (FP64, or FP32 in the mixed precisions): one CTA per node. col(., r) is an
-// unpivoted Householder QR whose first r columns are formed explicitly, then D_tau and the
-// parent's blocks. Since UU^* U = U, the product U^* D needed by the merge equals U^* T2^*
-// with T2 = (I - VV^*) Z Psi^+ and is taken from there; D V is formed from D. In FP64 the
-// merges into the parent's blocks run in a third kernel with several CTAs per node (column
-// chunks); the FP32 finish does them itself.
+// Finish kernels, per level after the side kernel: node_bases (col(., r): an unpivoted
+// Householder QR whose first r columns are formed by backward accumulation; FP64, or FP32 in the
+// mixed precisions), then D_tau from D = WY + U (Q - P - R V^*) (node_dblk_a / node_dblk_b in
+// FP64, over column blocks; node_dchain_f32 in FP32, which also forms U^* D and (D V)^*), then
+// the parent's blocks (node_merge / node_merge_f32, over column chunks).
 //
 // Reflectors use LAPACK's sign choice (beta = -sign(alpha) ||x||; identity when the tail is
 // zero) and are stored with their leading 1 explicit. Mapping: 256 threads = 32 groups of 8
-// lanes; a group owns one row (of the factored block, of a streamed sample row, or of a basis
-// column) and lane q of a group holds columns q, q + 8, ... Reductions inside a group take 3
-// shuffles. The FP64 pipe (2 DFMA per clock per SM on GB300) bounds the side kernel.
+// lanes; a group owns one row (of the factored block or of a streamed sample row) and lane q of
+// a group holds columns q, q + 8, ... Reductions inside a group take 3 shuffles. The FP64 pipe
+// (2 DFMA per clock per SM on GB300) bounds the side kernel where a level has many nodes.
 #include <algorithm>
 
 #include <cooperative_groups.h>
