@@ -18,7 +18,13 @@
  *  - Calls are asynchronous on `cuda_stream` unless stated. Argument and shape errors are
  *    detected on the host before anything is queued or allocated and are returned at once.
  *  - Numerical failures found on the device (a zero or non-finite pivot of a triangular
- *    factor) are recorded in a per-handle status word, read by hbs_sync_status().
+ *    factor) and bounded device-side waits that gave up are recorded in a status word (one per
+ *    handle for the sweep, one per device for the tensor-core sampling), read and cleared by
+ *    hbs_sync_status() / hbs_sample_sync(). A wait that gives up also ends the other waits of
+ *    the same run at once; the next run starts with that abort cleared, so a timeout never
+ *    cuts a later run short (its report stays until it is read).
+ *  - A handle belongs to the CUDA device that was current at hbs_plan; calls on it with
+ *    another device current return HBS_ERR_ARG.
  *  - Every non-OK return leaves a message for hbs_last_error() (per calling thread).
  *  - The tree is the one of Section 3.1: root I = [0, N); the left child of a node of n
  *    indices receives the first ceil(n/2); nodes are split while larger than leaf_max, all
@@ -221,8 +227,18 @@ int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count);
 int hbs_set_graph(hbs_handle* h, int enable);
 
 /* Waits for the handle's queued work (cudaStreamSynchronize on cuda_stream) and returns the
- * device status of its last execution: HBS_OK or HBS_ERR_NUMERIC. Clears the status word. */
+ * device status of its executions since the last call: HBS_OK, HBS_ERR_TIMEOUT if a bounded
+ * wait of the sweep gave up (the factors of that run are then invalid), or HBS_ERR_NUMERIC
+ * (zero or non-finite pivot). Clears the status word. */
 int hbs_sync_status(hbs_handle* h, void* cuda_stream);
+
+/* For tests of the status handling (not for production use): ORs `bits` (1 = numeric,
+ * 2 = timeout) into the status word of handle h -- or, with h == NULL, into the tensor-core
+ * sampling status of the current device, where that sampling has run -- exactly as a failing
+ * pivot or a device-side wait that gave up would leave it, without running any kernel. A
+ * timeout bit also raises the abort flag of the current run. Synchronous.
+ * Errors: HBS_ERR_ARG (unknown bits), HBS_ERR_CUDA. */
+int hbs_test_inject_status(hbs_handle* h, int32_t bits);
 
 /* Frees the handle and everything it owns (NULL-safe). The caller must make sure no queued
  * work still uses it. */
@@ -257,6 +273,15 @@ size_t hbs_factor_bytes(const hbs_handle* h);
 int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Measurement support (no counterpart in the paper): the FP64 (DFMA) and FP32 (FFMA) multiply-
+ * add throughput of the current GPU in TFLOP/s, timed with CUDA events around kernels that keep
+ * every SM's pipes busy with independent chains (a warm-up launch, then five). These are the
+ * denominators of the roofline fractions of the FP64-pipe and double-float kernels.
+ * Synchronizes cuda_stream; allocates 16 bytes. Errors: HBS_ERR_ARG, HBS_ERR_NOMEM, HBS_ERR_CUDA.
+ */
+int hbs_probe_peaks(double* fp64_tflops, double* fp32_tflops, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------------------
  * Apply without allocating (no counterpart in the paper; a service of this library).
  *
  * hbs_apply grows a device workspace with cudaMalloc the first time it needs more. Some callers
@@ -274,12 +299,17 @@ int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream);
  * L = 0), must not exceed HBS_APPLY_STATIC_MAX_TASKS; larger requests return
  * HBS_ERR_UNSUPPORTED with the limit in the message, before anything is queued.
  *
- * The first call on each device looks up the device addresses of the two arrays
- * (cudaGetSymbolAddress, with that device current) and checks the result; make that first call
- * before any stream capture. Every call on a device shares the same two arrays and they keep
- * the last call's contents (nothing in them needs to start at zero: every entry a call reads
- * it has written first). Calls whose GPU work overlaps in time -- on different streams, or from
- * several threads -- race on the arrays; queue them on one stream or order them yourself.
+ * Set-up: the device addresses of the two arrays are looked up (cudaGetSymbolAddress, with the
+ * device current, result checked) once per device, by hbs_plan on the device it plans for, or
+ * else by the first hbs_apply_static call on a device. That lookup loads the arrays onto the
+ * device, which then holds them (about 17.3 MiB) until the process exits, so plan (or make the
+ * first call) before another allocator takes the GPU's memory; when the first call does the
+ * set-up, make it before any stream capture. A call queues only kernels on cuda_stream: the
+ * work list is written into its fixed array by a kernel, with no host-to-device copy.
+ * Every call on a device shares the same two arrays and they keep the last call's contents
+ * (nothing in them needs to start at zero: every entry a call reads it has written first).
+ * Calls whose GPU work overlaps in time -- on different streams, or from several threads --
+ * race on the arrays; queue them on one stream or order them yourself.
  * Arguments and errors otherwise as hbs_apply.
  */
 #define HBS_APPLY_STATIC_MAX_DOUBLES 2097152   /* 16 MiB of FP64 workspace per device */

@@ -94,7 +94,10 @@ struct Height {
 
 struct hbs_handle {
   int precision = 0;
+  int device = -1;            // the CUDA device current at hbs_plan; every call must run there
   std::vector<Item> items;
+  hbs::ApplyNode* d_nodes = nullptr;   // per item, per node id: Algorithm 1's node table
+  std::vector<int64_t> node_base;      // first entry of each item's table in d_nodes
   double* arena = nullptr;
   size_t arena_doubles = 0;
   size_t factor_doubles = 0;
@@ -117,7 +120,6 @@ struct hbs_handle {
              ws == o.ws && st == o.st;
     }
   } apply_key;
-  std::vector<int> apply_sizes;                        // tasks per pass of that list
   // likewise for hbs_apply_batch and d_batch: direction, stream, workspace, then per item
   // (X, Out, columns)
   std::vector<uintptr_t> batch_key;
@@ -238,6 +240,7 @@ void free_handle(hbs_handle* h) {
   for (auto& H : h->heights) cudaFree(H.d_tasks);
   cudaFree(h->arena);
   cudaFree(h->d_status);
+  cudaFree(h->d_nodes);
   cudaFree(h->apply_ws);
   cudaFree(h->d_gemm);
   cudaFree(h->batch_ws);
@@ -251,6 +254,10 @@ void free_handle(hbs_handle* h) {
 cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
   const bool fp32_finish =
       h->precision == HBS_PREC_MIXED_BF16X3 || h->precision == HBS_PREC_MIXED_BF16X6;
+  // a new run: clear the abort flag an earlier run may have left (the report bits stay until
+  // hbs_sync_status reads them)
+  cudaError_t me = cudaMemsetAsync(h->d_status + hbs::kAbortWord, 0, sizeof(int), st);
+  if (me != cudaSuccess) return me;
   for (auto& H : h->heights) {
     cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
                                             H.max_s, fp32_finish, H.R, h->d_status, st);
@@ -299,6 +306,89 @@ int launch_sweep(hbs_handle* h, cudaStream_t st) {
   }
   e = cudaGraphLaunch(h->graph_exec, st);
   return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep graph launch");
+}
+
+}  // namespace
+
+// ---- hbs_apply_static: Algorithm 1 with workspace and work list in fixed device arrays -----
+
+namespace {
+
+// Held on every GPU where this module is loaded (the first cudaGetSymbolAddress below loads it
+// there), until the process exits. Host code may not take these names as device addresses: in
+// host code they are stand-ins, and the per-device addresses come from cudaGetSymbolAddress.
+static __device__ __align__(256) double g_static_apply_ws[HBS_APPLY_STATIC_MAX_DOUBLES];
+static __device__ __align__(256) GemmTask g_static_apply_tasks[HBS_APPLY_STATIC_MAX_TASKS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double* g_static_ws_ptr[kMaxDevices] = {};
+GemmTask* g_static_task_ptr[kMaxDevices] = {};
+
+// Device addresses of the two arrays on the current device (looked up once per device).
+int static_arrays(double** ws, GemmTask** tasks) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(HBS_ERR_UNSUPPORTED, "hbs_apply_static: device %d beyond %d", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ws_ptr[dev]) {
+    void* a = nullptr;
+    void* b = nullptr;
+    e = cudaGetSymbolAddress(&a, g_static_apply_ws);
+    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetSymbolAddress(workspace)");
+    e = cudaGetSymbolAddress(&b, g_static_apply_tasks);
+    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetSymbolAddress(work list)");
+    g_static_task_ptr[dev] = static_cast<GemmTask*>(b);
+    g_static_ws_ptr[dev] = static_cast<double*>(a);
+  }
+  *ws = g_static_ws_ptr[dev];
+  *tasks = g_static_task_ptr[dev];
+  return HBS_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Doubles of Algorithm 1's workspace for c columns: q-hat and u-hat of every node on levels
+// 1..L, r x c each.
+size_t apply_ws_doubles(const Item& it, int c) {
+  return 2 * ((size_t(2) << it.L) - 2) * size_t(it.r) * size_t(c);
+}
+
+// Tasks of Algorithm 1's work list: 2^(L+1) - 2 upward, 2^(L+1) - 1 downward (1 when L = 0).
+size_t apply_task_count(const Item& it) { return it.L == 0 ? 1 : (size_t(4) << it.L) - 3; }
+
+// The passes of a work list built by hbs::launch_build_apply_tasks, one launch each: upward
+// levels L .. 1, then downward levels 0 .. L (2^l tasks per pass).
+int launch_apply_passes(const Item& it, const GemmTask* tasks, int c, cudaStream_t st,
+                        const char* who) {
+  std::vector<int> sizes;
+  if (it.L == 0) {
+    sizes.push_back(1);
+  } else {
+    for (int l = it.L; l >= 1; --l) sizes.push_back(1 << l);
+    for (int l = 0; l <= it.L; ++l) sizes.push_back(1 << l);
+  }
+  size_t at = 0;
+  for (int cnt : sizes) {
+    cudaError_t e = hbs::launch_gemm_tasks_f64(tasks + at, cnt, c, st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    at += size_t(cnt);
+  }
+  return HBS_OK;
+}
+
+// Every call on a handle must run on the device the handle was planned on.
+int check_device(const hbs_handle* h, const char* who) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  if (dev != h->device)
+    return fail(HBS_ERR_ARG, "%s: current device %d, handle planned on device %d", who, dev, h->device);
+  return HBS_OK;
 }
 
 }  // namespace
@@ -451,6 +541,10 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
   }
   auto* h = new hbs_handle();
   h->precision = precision;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return cuda_fail(cudaGetLastError(), "hbs_plan: cudaGetDevice");
+  }
   h->items.resize(batch);
   size_t cursor = 0;
   // factors
@@ -507,18 +601,50 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
     free_handle(h);
     return fail(HBS_ERR_NOMEM, "arena of %zu bytes: %s", cursor * sizeof(double), cudaGetErrorString(e));
   }
-  e = cudaMalloc(&h->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  e = cudaMalloc(&h->d_status, hbs::kStatusWords * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, hbs::kStatusWords * sizeof(int));
   if (e != cudaSuccess) {
     free_handle(h);
     return fail(HBS_ERR_NOMEM, "status word: %s", cudaGetErrorString(e));
   }
+  // Algorithm 1's node table of every item (hbs_apply and hbs_apply_static build their work
+  // lists from it on the device)
+  std::vector<hbs::ApplyNode> nodes;
+  for (auto& it : h->items) {
+    h->node_base.push_back(int64_t(nodes.size()));
+    const int64_t count = int64_t(2) << it.L;
+    for (int64_t t = 0; t < count; ++t) {
+      hbs::ApplyNode nd{};
+      if (t >= 1) {
+        nd.off = it.off[t];
+        nd.n = int((it.L == 0) ? it.N : it.node_rows(t));
+        nd.oU = it.oU[t];
+        nd.oV = it.oV[t];
+        nd.oD = it.oD[t];
+      }
+      nodes.push_back(nd);
+    }
+  }
+  e = cudaMalloc(&h->d_nodes, nodes.size() * sizeof(hbs::ApplyNode));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->d_nodes, nodes.data(), nodes.size() * sizeof(hbs::ApplyNode),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_handle(h);
+    return fail(HBS_ERR_NOMEM, "node table: %s", cudaGetErrorString(e));
+  }
+  // the fixed arrays of hbs_apply_static on this device, looked up (and so loaded) now, while
+  // the plan may allocate; a failure here is reported by hbs_apply_static itself
+  double* sws = nullptr;
+  GemmTask* stk = nullptr;
+  if (static_arrays(&sws, &stk) != HBS_OK) cudaGetLastError();
   *out = h;
   return ok();
 }
 
 int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream) {
   if (!h || !probs) return fail(HBS_ERR_ARG, "hbs_execute: NULL argument");
+  if (check_device(h, "hbs_execute") != HBS_OK) return HBS_ERR_ARG;
   bool changed = !h->tasks_uploaded;
   for (size_t i = 0; i < h->items.size(); ++i) {
     Item& it = h->items[i];
@@ -565,21 +691,12 @@ int hbs_apply(hbs_handle* h, int32_t item, int trans, int32_t ncols, const doubl
               double* Out, void* cuda_stream) {
   if (!h || !X || !Out || ncols < 1 || item < 0 || item >= int(h->items.size()))
     return fail(HBS_ERR_ARG, "hbs_apply: bad arguments");
+  if (check_device(h, "hbs_apply") != HBS_OK) return HBS_ERR_ARG;
   const Item& it = h->items[item];
-  const int r = it.r, c = ncols;
+  const int c = ncols;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const double* A = h->arena;
   // workspace: q-hat and u-hat for every node on levels 1..L, level-major, r x c per node
-  std::vector<int64_t> qoff(it.L + 1, 0), uoff(it.L + 1, 0);
-  size_t need = 0;
-  for (int l = 1; l <= it.L; ++l) {
-    qoff[l] = int64_t(need);
-    need += (size_t(1) << l) * r * c;
-  }
-  for (int l = 1; l <= it.L; ++l) {
-    uoff[l] = int64_t(need);
-    need += (size_t(1) << l) * r * c;
-  }
+  const size_t need = apply_ws_doubles(it, c);
   if (need > h->apply_ws_doubles) {
     cudaFree(h->apply_ws);
     h->apply_ws = nullptr;
@@ -593,88 +710,24 @@ int hbs_apply(hbs_handle* h, int32_t item, int trans, int32_t ncols, const doubl
   // factors are addressed through the arena, whose contents may have changed, not its address)
   hbs_handle::ApplyKey key;
   key.item = item; key.trans = trans; key.ncols = c; key.X = X; key.Out = Out; key.ws = ws; key.st = st;
-  if (key == h->apply_key) {
-    size_t at = 0;
-    for (int cnt : h->apply_sizes) {
-      cudaError_t e = hbs::launch_gemm_tasks_f64(h->d_gemm + at, cnt, c, st);
-      if (e != cudaSuccess) return cuda_fail(e, "apply kernel");
-      at += size_t(cnt);
+  if (!(key == h->apply_key)) {
+    h->apply_key = hbs_handle::ApplyKey{};            // invalid until the new list is built
+    const size_t total = apply_task_count(it);
+    if (total > h->d_gemm_cap) {
+      cudaFree(h->d_gemm);
+      h->d_gemm = nullptr;
+      h->d_gemm_cap = 0;
+      cudaError_t e = cudaMalloc(&h->d_gemm, total * sizeof(GemmTask));
+      if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "apply task list: %s", cudaGetErrorString(e));
+      h->d_gemm_cap = total;
     }
-    return ok();
+    cudaError_t e = hbs::launch_build_apply_tasks(h->d_nodes + h->node_base[item], it.L, it.r, it.N,
+                                                  trans, c, h->arena, X, Out, ws, h->d_gemm, st);
+    if (e != cudaSuccess) return cuda_fail(e, "apply work list");
+    h->apply_key = key;
   }
-  h->apply_key = hbs_handle::ApplyKey{};              // invalid until the new list is uploaded
-  auto qhat = [&](int64_t t, int l) { return ws + qoff[l] + (t - (int64_t(1) << l)) * r * c; };
-  auto uhat = [&](int64_t t, int l) { return ws + uoff[l] + (t - (int64_t(1) << l)) * r * c; };
-  // bases: trans swaps U and V, and uses D^*
-  const std::vector<int64_t>& oIn = trans ? it.oU : it.oV;
-  const std::vector<int64_t>& oOut = trans ? it.oV : it.oU;
-  std::vector<std::vector<GemmTask>> passes;
-  if (it.L == 0) {
-    GemmTask g{};
-    g.A1 = A + it.oD[1]; g.lda1 = int(it.N); g.t1 = trans; g.k1 = int(it.N);
-    g.B1 = X; g.ldb1 = c; g.C = Out; g.ldc = c; g.m = int(it.N);
-    passes.push_back({g});
-  } else {
-    for (int l = it.L; l >= 1; --l) {                       // upward pass
-      std::vector<GemmTask> v;
-      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
-        GemmTask g{};
-        const int n = int(it.node_rows(t));
-        g.A1 = A + oIn[t]; g.lda1 = r; g.t1 = 1; g.k1 = n; g.m = r;
-        g.B1 = (l == it.L) ? X + it.off[t] * c : qhat(2 * t, l + 1);
-        g.ldb1 = c; g.C = qhat(t, l); g.ldc = c;
-        v.push_back(g);
-      }
-      passes.push_back(v);
-    }
-    for (int l = 0; l <= it.L; ++l) {                       // downward pass
-      std::vector<GemmTask> v;
-      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
-        GemmTask g{};
-        const int n = (l == 0) ? 2 * r : int(it.node_rows(t));
-        if (l == 0) {
-          g.A1 = A + it.oD[1]; g.lda1 = n; g.t1 = trans; g.k1 = n; g.m = n;
-          g.B1 = qhat(2, 1); g.ldb1 = c; g.C = uhat(2, 1); g.ldc = c;
-        } else {
-          g.A1 = A + oOut[t]; g.lda1 = r; g.t1 = 0; g.k1 = r; g.m = n;
-          g.B1 = uhat(t, l); g.ldb1 = c;
-          g.A2 = A + it.oD[t]; g.lda2 = n; g.t2 = trans; g.k2 = n;
-          if (l < it.L) {
-            g.B2 = qhat(2 * t, l + 1); g.ldb2 = c; g.C = uhat(2 * t, l + 1); g.ldc = c;
-          } else {
-            g.B2 = X + it.off[t] * c; g.ldb2 = c; g.C = Out + it.off[t] * c; g.ldc = c;
-          }
-        }
-        v.push_back(g);
-      }
-      passes.push_back(v);
-    }
-  }
-  size_t total = 0;
-  for (auto& p : passes) total += p.size();
-  if (total > h->d_gemm_cap) {
-    cudaFree(h->d_gemm);
-    h->d_gemm = nullptr;
-    h->d_gemm_cap = 0;
-    cudaError_t e = cudaMalloc(&h->d_gemm, total * sizeof(GemmTask));
-    if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "apply task list: %s", cudaGetErrorString(e));
-    h->d_gemm_cap = total;
-  }
-  std::vector<GemmTask> flat;
-  flat.reserve(total);
-  for (auto& p : passes) flat.insert(flat.end(), p.begin(), p.end());
-  cudaError_t e = cudaMemcpyAsync(h->d_gemm, flat.data(), total * sizeof(GemmTask),
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "apply task upload");
-  h->apply_sizes.clear();
-  size_t at = 0;
-  for (auto& p : passes) {
-    e = hbs::launch_gemm_tasks_f64(h->d_gemm + at, int(p.size()), c, st);
-    if (e != cudaSuccess) return cuda_fail(e, "apply kernel");
-    at += p.size();
-    h->apply_sizes.push_back(int(p.size()));
-  }
-  h->apply_key = key;
+  const int rc = launch_apply_passes(it, h->d_gemm, c, st, "apply kernel");
+  if (rc != HBS_OK) return rc;
   return ok();
 }
 
@@ -685,10 +738,32 @@ int hbs_sync_status(hbs_handle* h, void* cuda_stream) {
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
   int status = 0;
   e = cudaMemcpy(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, hbs::kStatusWords * sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "status read");
+  if (status & hbs::kStatusTimeout)
+    return fail(HBS_ERR_TIMEOUT, "a bounded device-side wait of the sweep gave up%s",
+                (status & hbs::kStatusNumeric) ? " (a zero or non-finite pivot was also met)" : "");
   if (status & hbs::kStatusNumeric)
     return fail(HBS_ERR_NUMERIC, "zero or non-finite pivot in a triangular factor");
+  return ok();
+}
+
+int hbs_test_inject_status(hbs_handle* h, int32_t bits) {
+  if (bits & ~(hbs::kStatusNumeric | hbs::kStatusTimeout))
+    return fail(HBS_ERR_ARG, "hbs_test_inject_status: unknown bits %d", bits);
+  if (!h) {
+    cudaError_t e = hbs::sample_tc_inject(bits);
+    if (e == cudaSuccess) e = hbs::sample_oz_inject(bits);
+    if (e != cudaSuccess) return cuda_fail(e, "hbs_test_inject_status");
+    return ok();
+  }
+  int now[hbs::kStatusWords];
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(now, h->d_status, sizeof(now), cudaMemcpyDeviceToHost);
+  now[0] |= bits;
+  if (bits & hbs::kStatusTimeout) now[hbs::kAbortWord] = 1;
+  if (e == cudaSuccess) e = cudaMemcpy(h->d_status, now, sizeof(now), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_test_inject_status");
   return ok();
 }
 
@@ -765,6 +840,7 @@ int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream) {
 int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* const* Out,
                     const int32_t* ncols, void* cuda_stream) {
   if (!h || !X || !Out || !ncols) return fail(HBS_ERR_ARG, "hbs_apply_batch: bad arguments");
+  if (check_device(h, "hbs_apply_batch") != HBS_OK) return HBS_ERR_ARG;
   const int nitems = int(h->items.size());
   int maxL = 0;
   size_t need = 0;
@@ -905,7 +981,10 @@ int hbs_apply_batch(hbs_handle* h, int trans, const double* const* X, double* co
 int hbs_autotune(hbs_handle* h, void* cuda_stream) {
   if (!h) return fail(HBS_ERR_ARG, "hbs_autotune: NULL handle");
   if (!h->tasks_uploaded) return fail(HBS_ERR_ARG, "hbs_autotune: execute the handle once first");
+  if (check_device(h, "hbs_autotune") != HBS_OK) return HBS_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t ce = cudaMemsetAsync(h->d_status + hbs::kAbortWord, 0, sizeof(int), st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "hbs_autotune: status");
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "hbs_autotune: events");
@@ -986,67 +1065,21 @@ int hbs_set_graph(hbs_handle* h, int enable) {
 
 }  // extern "C"
 
-// ---- hbs_apply_static: Algorithm 1 with workspace and work list in fixed device arrays -----
-
-namespace {
-
-// Reserved on every GPU that loads the library, until exit. Host code may not take these
-// names as device addresses: the per-device addresses come from cudaGetSymbolAddress below.
-static __device__ __align__(256) double g_static_apply_ws[HBS_APPLY_STATIC_MAX_DOUBLES];
-static __device__ __align__(256) GemmTask g_static_apply_tasks[HBS_APPLY_STATIC_MAX_TASKS];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-double* g_static_ws_ptr[kMaxDevices] = {};
-GemmTask* g_static_task_ptr[kMaxDevices] = {};
-
-// Device addresses of the two arrays on the current device (looked up once per device).
-int static_arrays(double** ws, GemmTask** tasks) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices)
-    return fail(HBS_ERR_UNSUPPORTED, "hbs_apply_static: device %d beyond %d", dev, kMaxDevices);
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ws_ptr[dev]) {
-    void* a = nullptr;
-    void* b = nullptr;
-    e = cudaGetSymbolAddress(&a, g_static_apply_ws);
-    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetSymbolAddress(workspace)");
-    e = cudaGetSymbolAddress(&b, g_static_apply_tasks);
-    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: cudaGetSymbolAddress(work list)");
-    g_static_task_ptr[dev] = static_cast<GemmTask*>(b);
-    g_static_ws_ptr[dev] = static_cast<double*>(a);
-  }
-  *ws = g_static_ws_ptr[dev];
-  *tasks = g_static_task_ptr[dev];
-  return HBS_OK;
-}
-
-}  // namespace
 
 extern "C" int hbs_apply_static(const hbs_handle* h, int32_t item, int trans, int32_t ncols,
                                 const double* X, double* Out, void* cuda_stream) {
   if (!h || !X || !Out || ncols < 1 || item < 0 || item >= int(h->items.size()))
     return fail(HBS_ERR_ARG, "hbs_apply_static: bad arguments");
+  if (check_device(h, "hbs_apply_static") != HBS_OK) return HBS_ERR_ARG;
   const Item& it = h->items[item];
-  const int r = it.r, c = ncols;
+  const int c = ncols;
   // size checks first: nothing is queued for a request beyond the fixed arrays
-  std::vector<int64_t> qoff(it.L + 1, 0), uoff(it.L + 1, 0);
-  size_t need = 0;
-  for (int l = 1; l <= it.L; ++l) {
-    qoff[l] = int64_t(need);
-    need += (size_t(1) << l) * r * c;
-  }
-  for (int l = 1; l <= it.L; ++l) {
-    uoff[l] = int64_t(need);
-    need += (size_t(1) << l) * r * c;
-  }
-  const size_t ntasks = (it.L == 0) ? 1 : (size_t(4) << it.L) - 3;
+  const size_t need = apply_ws_doubles(it, c);
+  const size_t ntasks = apply_task_count(it);
   if (need > size_t(HBS_APPLY_STATIC_MAX_DOUBLES))
     return fail(HBS_ERR_UNSUPPORTED,
                 "hbs_apply_static: workspace of %zu doubles exceeds the fixed %d (L=%d, r=%d, ncols=%d)",
-                need, HBS_APPLY_STATIC_MAX_DOUBLES, it.L, r, c);
+                need, HBS_APPLY_STATIC_MAX_DOUBLES, it.L, it.r, c);
   if (ntasks > size_t(HBS_APPLY_STATIC_MAX_TASKS))
     return fail(HBS_ERR_UNSUPPORTED, "hbs_apply_static: %zu node products exceed the fixed %d (L=%d)",
                 ntasks, HBS_APPLY_STATIC_MAX_TASKS, it.L);
@@ -1055,63 +1088,12 @@ extern "C" int hbs_apply_static(const hbs_handle* h, int32_t item, int trans, in
   const int rc = static_arrays(&ws, &d_tasks);
   if (rc != HBS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const double* A = h->arena;
-  auto qhat = [&](int64_t t, int l) { return ws + qoff[l] + (t - (int64_t(1) << l)) * r * c; };
-  auto uhat = [&](int64_t t, int l) { return ws + uoff[l] + (t - (int64_t(1) << l)) * r * c; };
-  const std::vector<int64_t>& oIn = trans ? it.oU : it.oV;
-  const std::vector<int64_t>& oOut = trans ? it.oV : it.oU;
-  std::vector<GemmTask> flat;
-  std::vector<int> pass_sizes;
-  flat.reserve(ntasks);
-  if (it.L == 0) {
-    GemmTask g{};
-    g.A1 = A + it.oD[1]; g.lda1 = int(it.N); g.t1 = trans; g.k1 = int(it.N);
-    g.B1 = X; g.ldb1 = c; g.C = Out; g.ldc = c; g.m = int(it.N);
-    flat.push_back(g);
-    pass_sizes.push_back(1);
-  } else {
-    for (int l = it.L; l >= 1; --l) {                       // upward pass
-      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
-        GemmTask g{};
-        const int n = int(it.node_rows(t));
-        g.A1 = A + oIn[t]; g.lda1 = r; g.t1 = 1; g.k1 = n; g.m = r;
-        g.B1 = (l == it.L) ? X + it.off[t] * c : qhat(2 * t, l + 1);
-        g.ldb1 = c; g.C = qhat(t, l); g.ldc = c;
-        flat.push_back(g);
-      }
-      pass_sizes.push_back(1 << l);
-    }
-    for (int l = 0; l <= it.L; ++l) {                       // downward pass
-      for (int64_t t = int64_t(1) << l; t < (int64_t(2) << l); ++t) {
-        GemmTask g{};
-        const int n = (l == 0) ? 2 * r : int(it.node_rows(t));
-        if (l == 0) {
-          g.A1 = A + it.oD[1]; g.lda1 = n; g.t1 = trans; g.k1 = n; g.m = n;
-          g.B1 = qhat(2, 1); g.ldb1 = c; g.C = uhat(2, 1); g.ldc = c;
-        } else {
-          g.A1 = A + oOut[t]; g.lda1 = r; g.t1 = 0; g.k1 = r; g.m = n;
-          g.B1 = uhat(t, l); g.ldb1 = c;
-          g.A2 = A + it.oD[t]; g.lda2 = n; g.t2 = trans; g.k2 = n;
-          if (l < it.L) {
-            g.B2 = qhat(2 * t, l + 1); g.ldb2 = c; g.C = uhat(2 * t, l + 1); g.ldc = c;
-          } else {
-            g.B2 = X + it.off[t] * c; g.ldb2 = c; g.C = Out + it.off[t] * c; g.ldc = c;
-          }
-        }
-        flat.push_back(g);
-      }
-      pass_sizes.push_back(1 << l);
-    }
-  }
-  // pageable source: the copy is staged before this call returns, nothing is allocated here
-  cudaError_t e = cudaMemcpyAsync(d_tasks, flat.data(), flat.size() * sizeof(GemmTask),
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: work list upload");
-  size_t at = 0;
-  for (int cnt : pass_sizes) {
-    e = hbs::launch_gemm_tasks_f64(d_tasks + at, cnt, c, st);
-    if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: apply kernel");
-    at += size_t(cnt);
-  }
+  // the work list is written into the fixed array by a kernel on the caller's stream: no host
+  // copy, no allocation
+  cudaError_t e = hbs::launch_build_apply_tasks(h->d_nodes + h->node_base[item], it.L, it.r, it.N,
+                                                trans, c, h->arena, X, Out, ws, d_tasks, st);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_apply_static: work list");
+  const int prc = launch_apply_passes(it, d_tasks, c, st, "hbs_apply_static: apply kernel");
+  if (prc != HBS_OK) return prc;
   return ok();
 }

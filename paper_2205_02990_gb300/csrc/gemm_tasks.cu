@@ -149,7 +149,62 @@ __global__ void __launch_bounds__(THREADS) gemm_tasks_f64(const GemmTask* __rest
   }
 }
 
+// One task of Algorithm 1's work list per thread (layout in hbs_internal.cuh).
+__global__ void build_apply_tasks(const ApplyNode* __restrict__ nodes, int L, int r, int64_t N,
+                                  int trans, int c, const double* arena, const double* X,
+                                  double* Out, double* ws, GemmTask* __restrict__ out) {
+  const int64_t up = (L == 0) ? 0 : (int64_t(2) << L) - 2;          // upward tasks
+  const int64_t total = (L == 0) ? 1 : up + (int64_t(2) << L) - 1;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int64_t rc = static_cast<int64_t>(r) * c;
+  auto qhat = [&](int64_t t) { return ws + (t - 2) * rc; };
+  auto uhat = [&](int64_t t) { return ws + up * rc + (t - 2) * rc; };
+  GemmTask g{};
+  if (L == 0) {                                                      // A = D
+    g.A1 = arena + nodes[1].oD; g.lda1 = static_cast<int>(N); g.t1 = trans;
+    g.k1 = static_cast<int>(N); g.m = static_cast<int>(N);
+    g.B1 = X; g.ldb1 = c; g.C = Out; g.ldc = c;
+  } else if (i < up) {                                               // upward: q-hat_t = V_t^* ..
+    int l = L;
+    while (i >= (int64_t(2) << L) - (int64_t(1) << l)) --l;          // levels L, L-1, .. in order
+    const int64_t t = (int64_t(1) << l) + (i - ((int64_t(2) << L) - (int64_t(2) << l)));
+    const ApplyNode nd = nodes[t];
+    g.A1 = arena + (trans ? nd.oU : nd.oV); g.lda1 = r; g.t1 = 1; g.k1 = nd.n; g.m = r;
+    g.B1 = (l == L) ? X + nd.off * c : qhat(2 * t);
+    g.ldb1 = c; g.C = qhat(t); g.ldc = c;
+  } else {                                                           // downward, node t = j + 1
+    const int64_t t = i - up + 1;
+    const int l = 63 - __clzll(static_cast<long long>(t));
+    const ApplyNode nd = nodes[t];
+    if (l == 0) {
+      g.A1 = arena + nd.oD; g.lda1 = nd.n; g.t1 = trans; g.k1 = nd.n; g.m = nd.n;
+      g.B1 = qhat(2); g.ldb1 = c; g.C = uhat(2); g.ldc = c;
+    } else {
+      g.A1 = arena + (trans ? nd.oV : nd.oU); g.lda1 = r; g.t1 = 0; g.k1 = r; g.m = nd.n;
+      g.B1 = uhat(t); g.ldb1 = c;
+      g.A2 = arena + nd.oD; g.lda2 = nd.n; g.t2 = trans; g.k2 = nd.n;
+      if (l < L) {
+        g.B2 = qhat(2 * t); g.ldb2 = c; g.C = uhat(2 * t); g.ldc = c;
+      } else {
+        g.B2 = X + nd.off * c; g.ldb2 = c; g.C = Out + nd.off * c; g.ldc = c;
+      }
+    }
+  }
+  out[i] = g;
+}
+
 }  // namespace
+
+cudaError_t launch_build_apply_tasks(const ApplyNode* nodes, int L, int r, int64_t N, int trans,
+                                     int c, const double* arena, const double* X, double* Out,
+                                     double* ws, GemmTask* out, cudaStream_t st) {
+  const int64_t total = (L == 0) ? 1 : (int64_t(4) << L) - 3;
+  const int64_t blocks = (total + THREADS - 1) / THREADS;
+  build_apply_tasks<<<static_cast<unsigned>(blocks), THREADS, 0, st>>>(nodes, L, r, N, trans, c,
+                                                                       arena, X, Out, ws, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st) {
   if (ntasks <= 0) return cudaSuccess;

@@ -8,8 +8,15 @@
 
 namespace hbs {
 
+// Device status block: two ints. Word 0 collects the report bits below until the host reads
+// and clears it. Word 1 is the abort flag of the current run: set together with the timeout bit
+// when a bounded wait gives up, so that the other CTAs of that run stop waiting too, and cleared
+// by the host at the start of every run (a memset queued before the run's first kernel), so
+// that a timeout left by an earlier run never cuts a later run short.
 constexpr int kStatusNumeric = 1;   // bit set in the device status word on a bad pivot
 constexpr int kStatusTimeout = 2;   // bit set when a bounded device-side wait gave up
+constexpr int kAbortWord = 1;       // index of the abort flag in the status block
+constexpr int kStatusWords = 2;
 
 // One node of Algorithm 2 for the per-level sweep kernel. All matrices are row-major.
 struct NodeTask {
@@ -44,6 +51,25 @@ struct GemmTask {
   int32_t t1, t2;                       // 1 = transpose
   int32_t ncols;                        // columns of C and B; 0 = the launch's ncols
 };
+
+// One node of a compressed problem, for building the work list of Algorithm 1 on the device:
+// first row, row count (2r above the leaves; N when the tree has one node) and the arena
+// offsets (doubles) of U, V (-1 at the root) and D.
+struct ApplyNode {
+  int64_t off;
+  int64_t oU, oV, oD;
+  int32_t n;
+  int32_t pad;
+};
+
+// Writes Algorithm 1's work list for one problem (depth L, rank r, N rows; nodes indexed by node
+// id) into out: the upward pass, levels L .. 1 (2^l node products each), then the downward pass,
+// levels 0 .. L (2^l each), 2^(L+2) - 3 tasks in all (1 when L = 0). q-hat and u-hat of node t
+// (levels >= 1) live in ws at (t - 2) r c and (2^(L+1) - 2 + t - 2) r c doubles (level-major,
+// r x c each). trans swaps U and V and uses D^*.
+cudaError_t launch_build_apply_tasks(const ApplyNode* nodes, int L, int r, int64_t N, int trans,
+                                     int c, const double* arena, const double* X, double* Out,
+                                     double* ws, GemmTask* out, cudaStream_t st);
 
 // Shared memory of the sweep kernels for a node of n rows (sweep.cu).
 size_t side_smem_doubles(int n, int s);
@@ -81,6 +107,9 @@ cudaError_t launch_sample_dense_tc(const float* A, int64_t lda, int64_t N, const
                                    const double* Ps, int s, double* Y, double* Z, int slices,
                                    int kchunk, cudaStream_t st);
 cudaError_t sample_tc_status(int* host_status, bool clear);
+// ORs report bits into the status block (a timeout bit also raises the abort flag), as a wait
+// that gave up would leave them; for tests of the host-side status handling.
+cudaError_t sample_tc_inject(int bits);
 // Column tiling shared by the tensor-core products: s <= 128 as one tile of s rounded up to 32,
 // wider s as tiles of 128 (sample_tc.cu).
 void column_tiles(int s, int* BN, int* BNt);
@@ -91,6 +120,7 @@ cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, cons
                                    const double* Ps, int s, double* Y, double* Z, int digits,
                                    cudaStream_t st);
 cudaError_t sample_oz_status(int* host_status, bool clear);
+cudaError_t sample_oz_inject(int bits);
 // ncols: the column count of every task (1 .. 4 takes the grouped skinny kernel), or 0 when each
 // task carries its own.
 cudaError_t launch_gemm_tasks_f64(const GemmTask* d_tasks, int ntasks, int ncols, cudaStream_t st);

@@ -140,10 +140,15 @@ __device__ __forceinline__ void offset_value(double x, int E, uint32_t& vl, uint
 template <int S>
 __device__ __forceinline__ uint32_t digit_pair_f16(uint32_t l0, uint32_t h0, uint32_t l1,
                                                    uint32_t h1, int i) {
-  static_assert(S >= 5 && S <= 7, "the leading digit sits in the high word");
+  static_assert(S >= 4 && S <= 7, "4 to 7 digits");
   const int k = S - 1 - i;                              // byte position from the bottom
   uint32_t w, mask = 0x00ff00ffu;
-  if (k == S - 1) {
+  if (S == 4 && k == S - 1) {                           // leading 9 bits straddle the two words
+    const uint32_t b0 = __funnelshift_r(l0, h0, 24) & 0x1ffu;
+    const uint32_t b1 = __funnelshift_r(l1, h1, 24) & 0x1ffu;
+    w = b0 | (b1 << 16);
+    mask = 0x01ff01ffu;
+  } else if (k == S - 1) {
     const uint32_t b = static_cast<uint32_t>(S - 5);    // leading byte in the high word
     w = __byte_perm(h0, h1, b | ((b + 1) << 4) | ((b + 4) << 8) | ((b + 5) << 12));
     mask = 0x01ff01ffu;
@@ -327,7 +332,9 @@ template <int S, int D>
 __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad)[S],
                                                const uint64_t (&bd)[S], uint32_t idesc,
                                                uint64_t* freed) {
-  if constexpr (D < S - 1) {
+  if constexpr (D >= S) {
+    return;                                             // no such diagonal (never called)
+  } else if constexpr (D < S - 1) {
 #pragma unroll
     for (int i = 0; i <= D; ++i)
 #pragma unroll
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             OzArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  if (aborted(a.status)) return;
+  if (aborted(a.status)) return;              // a CTA of this run timed out: nothing issued yet
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int BN = a.BN;
   const int tile_b = BN * 128;
@@ -666,6 +673,9 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
   auto* EP = reinterpret_cast<int16_t*>(base + off_ep);
   auto* rexp = reinterpret_cast<int*>(base + off_rexp);
   auto* partial = reinterpret_cast<float2*>(base + off_part);
+  // a new run: clear the abort flag an earlier run may have left (the report bits stay)
+  e = cudaMemsetAsync(status + kAbortWord, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
 
   oz_split_a<S><<<dim3(W, W), 256, 0, st>>>(A, lda, N, Yd, Zd, ldd, EY, EZ, W, status);
   oz_split_b<S><<<W, 256, 0, st>>>(Om, N, s, BNt, ldd, Bo, EO, status);
@@ -714,9 +724,13 @@ cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, cons
   int BN, BNt;
   column_tiles(s, &BN, &BNt);
   if (oz_smem_bytes(digits, BN) > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
-  if (digits == 6) return launch_products<6>(A, lda, N, Om, Ps, s, Y, Z, st);
-  if (digits == 7) return launch_products<7>(A, lda, N, Om, Ps, s, Y, Z, st);
-  return cudaErrorInvalidValue;
+  switch (digits) {
+    case 4: return launch_products<4>(A, lda, N, Om, Ps, s, Y, Z, st);
+    case 5: return launch_products<5>(A, lda, N, Om, Ps, s, Y, Z, st);
+    case 6: return launch_products<6>(A, lda, N, Om, Ps, s, Y, Z, st);
+    case 7: return launch_products<7>(A, lda, N, Om, Ps, s, Y, Z, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t sample_oz_status(int* host_status, bool clear) {
@@ -731,7 +745,26 @@ cudaError_t sample_oz_status(int* host_status, bool clear) {
   }
   if (!status) return cudaSuccess;
   e = cudaMemcpy(host_status, status, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && clear) e = cudaMemset(status, 0, sizeof(int));
+  if (e == cudaSuccess && clear) e = cudaMemset(status, 0, kStatusWords * sizeof(int));
+  return e;
+}
+
+cudaError_t sample_oz_inject(int bits) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int* status = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_oz_mutex);
+    if (dev < static_cast<int>(g_oz_scratch.size())) status = static_cast<int*>(g_oz_scratch[dev].ptr);
+  }
+  if (!status) return cudaSuccess;
+  const int words[kStatusWords] = {bits, (bits & kStatusTimeout) ? 1 : 0};
+  int now[kStatusWords];
+  e = cudaMemcpy(now, status, sizeof(now), cudaMemcpyDeviceToHost);
+  now[0] |= words[0];
+  now[kAbortWord] |= words[kAbortWord];
+  if (e == cudaSuccess) e = cudaMemcpy(status, now, sizeof(now), cudaMemcpyHostToDevice);
   return e;
 }
 

@@ -152,7 +152,7 @@ template <int P, int Q, bool TRANS, int SO, int DR>
 __global__ void __launch_bounds__(kTcThreads, 1)
     sliced_gemm_tc(const __grid_constant__ CUtensorMap tmB, TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  if (aborted(a.status)) return;              // a CTA of this or an earlier launch timed out
+  if (aborted(a.status)) return;              // a CTA of this run timed out: nothing issued yet
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int BN = a.BN;
   const int slice_b_bytes = BN * 128;
@@ -502,7 +502,26 @@ cudaError_t sample_tc_status(int* host_status, bool clear) {
   }
   if (!status) return cudaSuccess;
   e = cudaMemcpy(host_status, status, sizeof(int), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && clear) e = cudaMemset(status, 0, sizeof(int));
+  if (e == cudaSuccess && clear) e = cudaMemset(status, 0, kStatusWords * sizeof(int));
+  return e;
+}
+
+cudaError_t sample_tc_inject(int bits) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int* status = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_tc_mutex);
+    if (dev < static_cast<int>(g_tc_scratch.size())) status = static_cast<int*>(g_tc_scratch[dev].ptr);
+  }
+  if (!status) return cudaSuccess;
+  const int words[kStatusWords] = {bits, (bits & kStatusTimeout) ? 1 : 0};
+  int now[kStatusWords];
+  e = cudaMemcpy(now, status, sizeof(now), cudaMemcpyDeviceToHost);
+  now[0] |= words[0];
+  now[kAbortWord] |= words[kAbortWord];
+  if (e == cudaSuccess) e = cudaMemcpy(status, now, sizeof(now), cudaMemcpyHostToDevice);
   return e;
 }
 
@@ -530,6 +549,9 @@ cudaError_t launch_sample_dense_tc(const float* A, int64_t lda, int64_t N, const
   auto* bY = reinterpret_cast<__nv_bfloat16*>(static_cast<uint8_t*>(scratch) + 1024);
   auto* bZ = bY + 3 * BNt * ldb;
   double* partial = reinterpret_cast<double*>(bZ + 3 * BNt * ldb);
+  // a new run: clear the abort flag an earlier run may have left (the report bits stay)
+  e = cudaMemsetAsync(status + kAbortWord, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
 
   const dim3 tb(32, 8), tg(static_cast<unsigned>((ldb + 31) / 32), static_cast<unsigned>((BNt + 31) / 32));
   if (slices == 2) {

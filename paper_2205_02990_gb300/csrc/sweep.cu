@@ -450,6 +450,16 @@ __global__ void __launch_bounds__(THREADS, 2)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
   }
+  // A wait above that gave up (its own timeout, or the run's abort flag) may have left a copy
+  // into this CTA's shared memory in flight. Every owner sends every row it owns whatever its
+  // waits returned, so each armed row still lands: account for all of them, under one shared
+  // deadline, before the cluster may leave.
+  if (aborted(status)) {
+    const unsigned long long deadline = now_ns() + kWaitNs;
+    for (int i = threadIdx.x; i < n; i += THREADS)
+      if (i % C != c) mbar_wait_until(&bar[i], 0, status, deadline);
+  }
+  __syncthreads();
   // every CTA has received every row: no copy is in flight from or into any CTA of the cluster
   cl.sync();
   for (int j = threadIdx.x; j < n; j += THREADS) rdiag[j] = F[static_cast<size_t>(j) * ldF + s + 1];

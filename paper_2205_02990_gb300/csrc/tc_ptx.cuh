@@ -53,14 +53,20 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
   return done != 0;
 }
 
+// The abort flag of the current run (word kAbortWord of the status block).
 __device__ __forceinline__ bool aborted(const int* status) {
-  return (*reinterpret_cast<const volatile int*>(status) & kStatusTimeout) != 0;
+  return reinterpret_cast<const volatile int*>(status)[kAbortWord] != 0;
+}
+
+__device__ __forceinline__ void record_timeout(int* status) {
+  atomicOr(status, kStatusTimeout);
+  atomicExch(status + kAbortWord, 1);
 }
 
 // Wait for the phase with the given parity; false (and the timeout bit set) after kWaitNs, or,
-// when `abortable`, as soon as another CTA of the grid has recorded a timeout. Waits for work
-// that completes by itself (copies in flight, issued MMAs) are not abortable, so that the CTA
-// never frees tensor memory or exits under them.
+// when `abortable`, as soon as another CTA of the same run has recorded a timeout. Waits for
+// work that completes by itself (copies in flight, issued MMAs) are not abortable, so that the
+// CTA never frees tensor memory or exits under them.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* status,
                                           bool abortable = true) {
   if (mbar_test(b, parity)) return true;
@@ -68,7 +74,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* sta
   for (uint32_t i = 1;; ++i) {
     if (mbar_test(b, parity)) return true;
     if ((i & 255u) == 0 && (now_ns() - t0 > kWaitNs || (abortable && aborted(status)))) {
-      atomicOr(status, kStatusTimeout);
+      record_timeout(status);
+      return false;
+    }
+  }
+}
+
+// Not abortable, bounded by an absolute deadline (globaltimer ns) shared by several waits.
+__device__ __forceinline__ bool mbar_wait_until(uint64_t* b, uint32_t parity, int* status,
+                                                unsigned long long deadline) {
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_test(b, parity)) return true;
+    if ((i & 255u) == 255u && now_ns() > deadline) {
+      record_timeout(status);
       return false;
     }
   }

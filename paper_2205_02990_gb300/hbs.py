@@ -35,7 +35,8 @@ EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan"
             "hbs_apply", "hbs_sync_status", "hbs_free", "hbs_last_error", "hbs_tree",
             "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
             "hbs_apply_static", "hbs_sample_sync", "hbs_apply_batch", "hbs_load_factors",
-            "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph"]
+            "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph",
+            "hbs_test_inject_status", "hbs_probe_peaks"]
 
 
 class HBSError(RuntimeError):
@@ -92,6 +93,8 @@ def load():
         "hbs_apply": (c.c_int, [c.c_void_p, c.c_int32, c.c_int, c.c_int32, c.c_void_p, c.c_void_p,
                                 c.c_void_p]),
         "hbs_sync_status": (c.c_int, [c.c_void_p, c.c_void_p]),
+        "hbs_test_inject_status": (c.c_int, [c.c_void_p, c.c_int32]),
+        "hbs_probe_peaks": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_double), c.c_void_p]),
         "hbs_free": (None, [c.c_void_p]),
         "hbs_last_error": (c.c_char_p, []),
         "hbs_tree": (c.c_int, [c.c_void_p, c.c_int32, c.POINTER(c.c_int32), c.c_void_p, c.c_void_p]),
@@ -356,6 +359,20 @@ def factor_layout(N, r, leaf_max):
 
 def hbs_sync_status(handle):
     _check(load().hbs_sync_status(handle.ptr, _stream()))
+
+
+def hbs_test_inject_status(handle, bits):
+    """Tests only: OR ``bits`` (1 numeric, 2 timeout) into the status word of ``handle`` (or,
+    with ``handle=None``, of the current device's tensor-core sampling) as a device-side failure
+    would, without running a kernel."""
+    _check(load().hbs_test_inject_status(None if handle is None else handle.ptr, bits))
+
+
+def hbs_probe_peaks():
+    """(FP64, FP32) multiply-add throughput of the current GPU in TFLOP/s (measured now)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().hbs_probe_peaks(ctypes.byref(a), ctypes.byref(b), _stream()))
+    return a.value, b.value
 
 
 def hbs_free(handle):
