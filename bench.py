@@ -37,12 +37,12 @@ UNIT = "N*s/s"
 N_DEF, R_DEF, S_DEF, LEAF_DEF, SEED = 32768, 40, 120, 64, 220502990 + 200
 SM_COUNT_GB300 = 152
 FP64_DFMA_PER_CLK_PER_SM = 2          # GB300: FP64 at 1/64 of the FP32 rate (1.25 TF nominal)
-FP64_PROBE_TFLOPS = 1.056             # measured DFMA throughput on this GB300 (see profiles/)
 GEMM_READ_8192 = 549.46e6             # dram bytes read by one sample_gemm_f64 launch, N = 8192
 GEMM_WRITE_8192 = 42.30e6             # dram bytes written (split-K partials) by that launch
 BF16_TFLOPS_SUSTAINED = 1666.9        # measured dense bf16 peak on this machine's GB300 (sustained)
 HBM_GBS = 6782.1                      # measured copy bandwidth on this machine's GB300
 FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # derived FP64 peak: SMs x DFMA/clk x 2 flop x clock
+DF32_SLOTS = 15                       # FP32 instructions of one double-float multiply-add
 
 
 def tree_nodes(N, leaf):
@@ -53,7 +53,8 @@ def tree_nodes(N, leaf):
 
 
 def node_flops(n, r, s, root=False):
-    """Algorithmic FP64 flops of one node of the sweep (Householder counts)."""
+    """Algorithmic flops of one node of the sweep (Householder counts; the D and merge terms in
+    the form the reduced-precision finish evaluates them, 12 r n^2 + 12 n r s)."""
     lq = 2 * n * n * (s - n / 3)                 # QR of Omega_tau^* (s x n)
     stream = 4 * n * n * s - 2 * n ** 3          # n rows through n reflectors
     solve = n ** 3                               # rows of Y Omega^+ against L_1
@@ -80,6 +81,55 @@ def sweep_flops(N, r, s, leaf):
         else:
             total += cnt * node_flops(2 * r, r, s)
     return total
+
+
+# Per-phase flops of one node, in the form each kernel evaluates the step (Algorithm 2):
+# side = LQ of one test block + its n sample rows through the reflectors + the solve with L_1;
+# bases = col(., r) of one side; D and merges as the FP64 finish forms them (P, Q, R, M, D; then
+# S - op(D) T and the two basis products per pass) or as the reduced finishes do (D with U^* D
+# and (D V)^*, then [B^*, -H][S; T]).
+def side_flops(n, s):
+    return 2 * n * n * (s - n / 3) + (4 * n * n * s - 2 * n ** 3) + n ** 3
+
+
+def bases_flops(n, r):
+    return 2 * r * r * (n - r / 3) + 4 * n * r * r - 4 * r ** 3 / 3
+
+
+def d_flops(n, r, reduced):
+    return 12 * r * n * n if reduced else 6 * r * n * n + 4 * r * r * n
+
+
+def merge_flops(n, r, s, reduced):
+    return 12 * n * r * s if reduced else 4 * n * n * s + 8 * n * r * s
+
+
+def sweep_phase_flops(N, r, s, leaf, reduced):
+    """Per height (finest first): flops of the side, bases, D and merge phases."""
+    L = tree_nodes(N, leaf)
+    out = []
+    for level in range(L, -1, -1):
+        cnt = 2 ** level
+        if level == L and L > 0:
+            big, small = -(-N // cnt), N // cnt
+            n_big = N - small * cnt
+            groups = [(big, n_big), (small, cnt - n_big)]
+        elif level == 0:
+            groups = [(2 * r if L > 0 else N, 1)]
+        else:
+            groups = [(2 * r, cnt)]
+        if level == 0:
+            n = groups[0][0]
+            out.append([side_flops(n, s), 0.0, 0.0, 0.0])
+            continue
+        ph = [0.0, 0.0, 0.0, 0.0]
+        for n, c in groups:
+            ph[0] += c * 2 * side_flops(n, s)
+            ph[1] += c * 2 * bases_flops(n, r)
+            ph[2] += c * d_flops(n, r, reduced)
+            ph[3] += c * merge_flops(n, r, s, reduced)
+        out.append(ph)
+    return out
 
 
 class ClockSampler:
@@ -136,6 +186,56 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def gpu_host_numa(gpu_id):
+    """NUMA node of the GPU's PCI device and the CPUs of that node (from sysfs), if known."""
+    info = {"gpu_numa_node": None, "node_cpus": None, "process_cpus": None}
+    try:
+        info["process_cpus"] = len(os.sched_getaffinity(0))
+        bus = subprocess.run(["nvidia-smi", "-i", str(gpu_id), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().lower()
+        if bus:
+            bus = bus[-12:] if len(bus) > 12 else bus          # domain:bus:dev.fn
+            path = f"/sys/bus/pci/devices/{bus}/numa_node"
+            if os.path.exists(path):
+                node = int(open(path).read().strip())
+                info["gpu_numa_node"] = node
+                if node >= 0:
+                    cl = open(f"/sys/devices/system/node/node{node}/cpulist").read().strip()
+                    cpus = set()
+                    for part in cl.split(","):
+                        a, _, b = part.partition("-")
+                        cpus.update(range(int(a), int(b or a) + 1))
+                    info["node_cpus"] = sorted(cpus)
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return info
+
+
+class numa_local:
+    """Runs the block on the CPUs of the GPU's NUMA node (so that pages pinned there are local to
+    the GPU), then restores the affinity."""
+
+    def __init__(self, info):
+        self.cpus = info.get("node_cpus")
+        self.saved = None
+
+    def __enter__(self):
+        if self.cpus:
+            try:
+                self.saved = os.sched_getaffinity(0)
+                allowed = set(self.cpus) & self.saved
+                if allowed:
+                    os.sched_setaffinity(0, allowed)
+            except OSError:
+                self.saved = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved:
+            os.sched_setaffinity(0, self.saved)
 
 
 def dist_env():
@@ -226,7 +326,61 @@ MODES = {
                  what="A stored FP64; FP64-class products from 7 exact 8-bit digits per entry "
                       "(28 FP16 digit-pair products on tcgen05 tensor cores, exact FP32 sums); "
                       "FP64 sweep"),
+    "cmp": dict(sample=4, sweep=4, a="f64",
+                what="A stored FP64; products from 5 exact 8-bit digits per entry (15 FP16 "
+                     "digit-pair products on tcgen05 tensor cores, exact FP32 sums); sweep with "
+                     "FP64 nullspace LQ / pseudo-inverse and bases, double-float (compensated "
+                     "FP32) D_tau and merges"),
+    "mixed3": dict(sample=1, sweep=1, a="f32",
+                   what="A stored FP32; bf16x3 products on tcgen05 tensor cores; sweep with FP64 "
+                        "nullspace QR / pseudo-inverse and FP32 bases, D_tau and merges"),
 }
+FINISH = {0: "fp64", 1: "fp32", 2: "fp32", 3: "fp64", 4: "df32"}
+
+
+def peaks_now(hb):
+    """Pipe peaks: derived from the unit counts and the 2070 MHz maximum clock, and measured now
+    by the library's FMA-chain probe (hbs_probe_peaks)."""
+    fp64_probe, fp32_probe = hb.hbs_probe_peaks()
+    fp32 = SM_COUNT_GB300 * 128 * 2 * 2070e6 / 1e12
+    return {"fp64_derived": FP64_TFLOPS, "fp32_derived": fp32,
+            "df32_derived": fp32 / DF32_SLOTS, "fp64_probe": fp64_probe, "fp32_probe": fp32_probe,
+            "df32_from_probe": fp32_probe / DF32_SLOTS}
+
+
+def sweep_roofline(phase_ms, N, r, s, leaf, finish, peaks):
+    """Roofline of the sweep's four phases from a hbs_profile_sweep run: algorithmic flops
+    (sweep_phase_flops) per height and phase over the CUDA-event time, against the derived peak
+    of the pipe each phase runs on (FP64; FP32 for the plain mixed finish; double-float: the FP32
+    peak over the 15 FP32 instructions of one double-float multiply-add)."""
+    reduced = finish != "fp64"
+    flops = sweep_phase_flops(N, r, s, leaf, reduced)
+    names = ("side", "bases", "D", "merge")
+    pipe = {"side": "fp64", "bases": "fp32" if finish == "fp32" else "fp64",
+            "D": finish, "merge": finish}
+    peak = {p: peaks[p + "_derived"] for p in ("fp64", "fp32", "df32")}
+    per_kernel = {}
+    for k, nm in enumerate(names):
+        ms = sum(h[k] for h in phase_ms)
+        fl = sum(f[k] for f in flops)
+        ach = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        per_kernel[nm] = {"ms": ms, "gflop": fl / 1e9, "achieved_tflops": ach,
+                          "pipe": pipe[nm], "peak_tflops": peak[pipe[nm]],
+                          "frac": ach / peak[pipe[nm]],
+                          "frac_by_height": [round((f[k] / (h[k] * 1e-3) / 1e12) / peak[pipe[nm]], 3)
+                                             if h[k] > 0 and f[k] > 0 else None
+                                             for h, f in zip(phase_ms, flops)],
+                          "ms_by_height": [round(h[k], 4) for h in phase_ms]}
+    tot_ms = sum(sum(h) for h in phase_ms)
+    tot_fl = sum(sum(f) for f in flops)
+    return {"finish": finish, "per_kernel": per_kernel,
+            "total": {"ms": tot_ms, "gflop": tot_fl / 1e9,
+                      "achieved_tflops": tot_fl / (tot_ms * 1e-3) / 1e12,
+                      "frac_of_fp64_peak": tot_fl / (tot_ms * 1e-3) / 1e12 / peak["fp64"]},
+            "peak_source": "derived: 152 SMs x (2 DFMA | 128 FFMA)/clk x 2 flop x 2070 MHz; "
+                           "double-float = FP32 / 15 instructions per multiply-add",
+            "timing": "CUDA events between the launches of one extra sweep with plain launches "
+                      "(hbs_profile_sweep)"}
 
 
 def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
@@ -270,7 +424,7 @@ def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
     out = {"items": items, "total_N_s": total_ns,
            "shapes": "N in {2048,4096,8192,16384}, k in [8,32], r=k+5, s=3r, leaf=pow2<=2r",
            "heights": None}
-    for name, prec in (("fp64", 0), ("mixed", 2)):
+    for name, prec in (("fp64", 0), ("compensated", 4), ("mixed", 2)):
         h = hb.hbs_plan(probs, precision=prec)
         hb.hbs_execute(h, probs)
         hb.hbs_autotune(h)
@@ -305,6 +459,88 @@ def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
                      "tuned_row_slices": hb.hbs_get_tuning(h)}
         h.free()
     gen.free()
+    return out
+
+
+def run_config3(hb, torch, steps, warmup, N=65536, r=R_DEF, s=S_DEF, leaf=LEAF_DEF,
+                seed=SEED + 300):
+    """The mixed-precision workload at N = 65536 (log kernel, r = 40, s = 120, leaf 64): "mixed"
+    (A stored FP32, 17.2 GB; bf16x6 products; FP32 bases, D_tau, merges around the FP64 LQ),
+    "mixed3" (the same with bf16x3 products, the split the workload names) and "cmp" (A stored
+    FP64; 5-digit products; double-float D_tau and merges), each timed per step (draws, products,
+    sweep) and held against the dense A and against the FP64 result (FP64-pipe products and FP64
+    sweep, run once) by 20 power steps (Section 5). Device-timed, A resident and streamed every
+    step (larger than L2)."""
+    from hbs_inputs import log_kernel_torch
+    A = log_kernel_torch(N, "cuda")
+    Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
+    prob = hb.Problem(N, r, s, leaf, Om, Ps, Y, Z)
+    out = {"N": N, "r": r, "s": s, "leaf": leaf, "A_fp64_gb": A.numel() * 8 / 1e9,
+           "A_fp32_gb": A.numel() * 4 / 1e9}
+
+    def draw():
+        hb.hbs_draw_gaussian(N, s, 0, seed, Om)
+        hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
+
+    def power_norm(apply_B, apply_Bt, nsteps=20):
+        g = torch.Generator(device="cuda").manual_seed(3)
+        v = torch.randn((N, 1), dtype=torch.float64, device="cuda", generator=g)
+        for _ in range(nsteps):
+            v = apply_Bt(apply_B(v / torch.linalg.norm(v)))
+        return float(torch.sqrt(torch.linalg.norm(v)))
+
+    def apply_h(h, x, trans=False):
+        o = torch.empty_like(x)
+        hb.hbs_apply(h, x, o, trans=trans)
+        return o
+
+    draw()
+    hb.hbs_sample_products(A, s, Om, Ps, Y, Z, precision=0)
+    h64 = hb.hbs_compress([prob], precision=0)
+    hb.hbs_sync_status(h64)
+    nA = power_norm(lambda x: A @ x, lambda x: A.T @ x)
+    n64 = power_norm(lambda x: apply_h(h64, x), lambda x: apply_h(h64, x, True))
+    out["fp64_once"] = {"rel_error": power_norm(lambda x: apply_h(h64, x) - A @ x,
+                                                lambda x: apply_h(h64, x, True) - A.T @ x) / nA}
+    A32 = None
+    for mode in ("mixed", "mixed3", "cmp"):
+        cfg = MODES[mode]
+        if cfg["a"] == "f32" and A32 is None:
+            A32 = A.float()
+        Aop = A if cfg["a"] == "f64" else A32
+        h = hb.hbs_plan([prob], precision=cfg["sweep"])
+        draw()
+        hb.hbs_sample_products(Aop, s, Om, Ps, Y, Z, precision=cfg["sample"])
+        hb.hbs_execute(h, [prob])
+        hb.hbs_autotune(h)
+
+        def step():
+            draw()
+            hb.hbs_sample_products(Aop, s, Om, Ps, Y, Z, precision=cfg["sample"])
+            hb.hbs_execute(h, [prob])
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        hb.hbs_sync_status(h)
+        hb.hbs_sample_sync()
+        ms = e0.elapsed_time(e1) / steps
+        out[mode] = {"ms_per_step": ms, "value": N * s / (ms / 1e3), "steps": steps,
+                     "rel_error": power_norm(lambda x: apply_h(h, x) - A @ x,
+                                             lambda x: apply_h(h, x, True) - A.T @ x) / nA,
+                     "vs_fp64": power_norm(lambda x: apply_h(h, x) - apply_h(h64, x),
+                                           lambda x: apply_h(h, x, True) - apply_h(h64, x, True)) / n64,
+                     "what": cfg["what"]}
+        h.free()
+    h64.free()
+    del A, A32, Om, Ps, Y, Z
+    torch.cuda.empty_cache()
     return out
 
 
@@ -371,7 +607,7 @@ def run_scaling(hb, torch, logN_list, k=45, r=50, s=150, leaf=64, seed=SEED + 50
 
         draw_and_sample()
         row = {"N": N}
-        for name, prec in (("fp64", 0), ("mixed", 2)):
+        for name, prec in (("fp64", 0), ("compensated", 4), ("mixed", 2)):
             h = hb.hbs_plan([prob], precision=prec)
             hb.hbs_execute(h, [prob])
             hb.hbs_sync_status(h)
@@ -418,6 +654,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the N = 65536 mixed-precision workload")
     ap.add_argument("--workload", default="logkernel",
                     choices=["logkernel", "doublelayer", "scaling", "batched", "apply"],
                     help="logkernel: the timed N = 32768 log-kernel step (default); doublelayer: "
@@ -483,7 +721,8 @@ def main():
         return float(t.item())
 
     stream = torch.cuda.current_stream()
-    modes = only or ["fp64", "oz64", "mixed", "tc64"]
+    modes = only or ["fp64", "oz64", "cmp", "mixed", "tc64"]
+    peaks = peaks_now(hb)
     A = (double_layer_torch if args.workload == "doublelayer" else log_kernel_torch)(N, "cuda")
     A32 = A.float() if any(MODES[m]["a"] == "f32" for m in modes) else None
     Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
@@ -537,8 +776,10 @@ def main():
         hb.hbs_sample_sync()
         elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3)
         per_launch = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * steps)
+        phases = hb.hbs_profile_sweep(h)                   # one more sweep, events per launch
         return dict(h=h, step=step, elapsed=elapsed, per_launch=per_launch,
-                    clocks=clk.summary() if clk else None, tuning=hb.hbs_get_tuning(h))
+                    clocks=clk.summary() if clk else None, tuning=hb.hbs_get_tuning(h),
+                    sweep=sweep_roofline(phases, N, r, s, leaf, FINISH[cfg["sweep"]], peaks))
 
     def power_norm(apply_B, apply_Bt, steps=20):
         g = torch.Generator(device="cuda").manual_seed(3)
@@ -580,9 +821,11 @@ def main():
         h = res["h"]
         cfg = MODES[head]
         src = A if cfg["a"] == "f64" else A32
-        A_host = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
-        A_host.copy_(src)
-        F_host = torch.empty(hb.hbs_factor_bytes(h), dtype=torch.uint8, pin_memory=True)
+        host_info = gpu_host_numa(gpu_id)
+        with numa_local(host_info):                 # pinned pages on the GPU's own memory node
+            A_host = torch.empty(src.shape, dtype=src.dtype, pin_memory=True)
+            A_host.copy_(src)
+            F_host = torch.empty(hb.hbs_factor_bytes(h), dtype=torch.uint8, pin_memory=True)
         dst = src                                   # the device copy the step multiplies
         streamed = cfg["sample"] == 0               # FP64 products take the pinned A directly
 
@@ -603,7 +846,24 @@ def main():
         e1.record(stream)
         barrier()
         te = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+        # the copies alone: all of A host -> device, and the factors device -> host
+        c = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        c[0].record(stream)
+        dst.copy_(A_host, non_blocking=True)
+        c[1].record(stream)
+        hb.hbs_copy_factors(h, F_host)
+        c[2].record(stream)
+        barrier()
+        h2d_ms, d2h_ms = c[0].elapsed_time(c[1]), c[1].elapsed_time(c[2])
+        a_bytes = src.numel() * src.element_size()
+        e2e_ms = te / args.steps * 1e3
+        dev_ms = res["elapsed"] / args.steps * 1e3
         e2e = {"value": world * N * s * args.steps / te, "unit": UNIT,
+               "ms_per_step": e2e_ms, "device_ms_per_step": dev_ms,
+               "overhead_ms_per_step": e2e_ms - dev_ms,
+               "h2d_ms_all_of_A": h2d_ms, "h2d_gbs": a_bytes / h2d_ms / 1e6,
+               "d2h_ms_factors": d2h_ms, "d2h_gbs": hb.hbs_factor_bytes(h) / d2h_ms / 1e6,
+               "host": {k: (len(v) if isinstance(v, list) else v) for k, v in host_info.items()},
                "a_transfer": "A streamed from pinned host memory by the library, copies overlapping "
                              "the products" if streamed else "A copied to the device before the call",
                "h2d_bytes_per_step": src.numel() * src.element_size(),
@@ -611,11 +871,12 @@ def main():
 
     value = world * N * s * args.steps / res["elapsed"]
     flops_product = 2.0 * N * N * s                          # one of the two products
-    if MODES[head]["sample"] == 3:
+    if MODES[head]["sample"] in (3, 4):
+        pairs = 28 if MODES[head]["sample"] == 3 else 15
         peak = BF16_TFLOPS_SUSTAINED
-        achieved = 28 * flops_product / res["per_launch"] / 1e12
-        roofline = {"kernel": "digit products per FP64 product (oz_split_a/b + oz_gemm + oz_reduce; "
-                              "28 exact FP16 digit-pair products)",
+        achieved = pairs * flops_product / res["per_launch"] / 1e12
+        roofline = {"kernel": f"digit products per FP64 product (oz_split_a/b + oz_gemm + oz_reduce; "
+                              f"{pairs} exact FP16 digit-pair products)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
                     "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
@@ -628,7 +889,8 @@ def main():
                     "traffic_source": "ncu capture at N=8192: reads (A) scaled by (N/8192)^2, "
                                       "writes (split partials) by N/8192",
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
-                    "probe_peak": FP64_PROBE_TFLOPS}
+                    "probe_peak": peaks["fp64_probe"],
+                    "probe_source": "hbs_probe_peaks: DFMA chains on every SM, measured in this run"}
     else:
         peak = BF16_TFLOPS_SUSTAINED
         achieved = 6 * flops_product / res["per_launch"] / 1e12
@@ -641,7 +903,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "oz64": "f64 (exact FP16 digit products)", "mixed": "bf16x6/f32/f64",
-                  "tc64": "bf16x6/f64"}[head], "data": "synthetic",
+                  "tc64": "bf16x6/f64", "cmp": "fp16 digits/df32/f64",
+                  "mixed3": "bf16x3/f32/f64"}[head], "data": "synthetic",
         "config": {"workload": ("double-layer BIE" if args.workload == "doublelayer" else "log-kernel")
                                + f" N={N} r={r} s={s} leaf={leaf} dense",
                    "N": N, "r": r, "s": s, "leaf": leaf, "levels": L + 1, "mode": head,
@@ -656,26 +919,34 @@ def main():
         # splits + 2 GEMMs + 2 reductions; digits: 2 test-matrix splits + 1 A split + 2 GEMMs +
         # 2 reductions), then per tree level the side, bases, D and merge kernels (FP64: D in two
         # kernels; FP32: one)
-        "gpu_launches": args.steps * ({0: 2 + 2 + 2, 2: 2 + 6, 3: 2 + 3 + 4}[MODES[head]["sample"]]
-                                      + (4 if MODES[head]["sweep"] in (1, 2) else 5) * (L + 1)),
-        "roofline": roofline,
+        "gpu_launches": args.steps * ({0: 2 + 2 + 2, 1: 2 + 6, 2: 2 + 6, 3: 2 + 3 + 4,
+                                       4: 2 + 3 + 4}[MODES[head]["sample"]]
+                                      + (4 if MODES[head]["sweep"] in (1, 2, 4) else 5) * (L + 1)),
+        "roofline": dict(roofline, sweep=res["sweep"]),
+        "peaks": peaks,
         "clocks": res["clocks"],
         "modes": {m: {"ms_per_step": rr["elapsed"] / args.steps * 1e3,
                       "value": world * N * s * args.steps / rr["elapsed"],
                       "rel_error": rr.get("rel_error"), "vs_fp64": rr.get("vs_fp64"),
                       "products_ms_per_launch": rr["per_launch"] * 1e3,
+                      "sweep_ms": rr["sweep"]["total"]["ms"],
+                      "sweep_frac_by_kernel": {k: round(v["frac"], 3)
+                                               for k, v in rr["sweep"]["per_kernel"].items()},
                       "tuned_row_slices": rr["tuning"],
                       "what": MODES[m]["what"]} for m, rr in results.items()},
     }
     if e2e:
         line["e2e"] = e2e
-    if not args.only and not args.no_batched and args.workload == "logkernel":
+    if not args.only and args.workload == "logkernel" and (not args.no_batched or not args.no_config3):
         for rr in results.values():
             rr["h"].free()
         results = {}
         del A, A32
         torch.cuda.empty_cache()
-        line["batched"] = run_batched(hb, torch)
+        if not args.no_config3:
+            line["config3"] = run_config3(hb, torch, min(args.steps, 5), 3)
+        if not args.no_batched:
+            line["batched"] = run_batched(hb, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, sample = oracle_sample_time(N, r, s, leaf, workload=args.workload)
         line["cpu_baseline"] = {"value": N * s / t_cpu, "unit": UNIT, "cores": cpu_cores(),

@@ -58,7 +58,7 @@ typedef enum {
                                3 slice products on the tensor cores, FP32 accumulation over
                                chunks of 2048, chunks summed in FP64 (~16 significant bits) */
   HBS_PREC_MIXED_BF16X6 = 2,/* as above with 3 slices and 6 products (~24 significant bits) */
-  HBS_PREC_FP64_TC = 3      /* sampling: FP64 A and Omega written as 7 exact 8-bit digits per
+  HBS_PREC_FP64_TC = 3,     /* sampling: FP64 A and Omega written as 7 exact 8-bit digits per
                                entry (one exponent per 64-wide block; an error-free splitting in
                                the manner of Ozaki et al., Numer. Algorithms 59, 2012), the 28
                                digit-pair products with exactly representable FP32 sums on the
@@ -66,6 +66,15 @@ typedef enum {
                                beyond: FP64-class products (~55-bit terms). Sweep in FP64 as
                                HBS_PREC_FP64. Needs N <= 2^20 and about 28 N^2 bytes of device
                                scratch (the digit planes of A in both orientations) */
+  HBS_PREC_MIXED_COMPENSATED = 4
+                            /* sampling: as HBS_PREC_FP64_TC with 5 digits per entry (15
+                               digit-pair products, terms to ~2^-38 of the block maxima; needs
+                               about 20 N^2 bytes of scratch). Sweep: the LQ of each test block
+                               (nullspace, pseudo-inverse) and the bases in FP64, D_tau and the
+                               parent blocks in double-float arithmetic (pairs of FP32 numbers,
+                               ~48 significant bits, FP32 exponent range: every intermediate
+                               of those products must stay within about 1e-30 .. 1e38 in
+                               magnitude) on the FP32 pipe */
 } hbs_precision;
 
 typedef enum { HBS_F64 = 0, HBS_F32 = 1 } hbs_dtype;
@@ -110,9 +119,9 @@ typedef struct {
 } hbs_operator;
 
 /* Precision of the products (hbs_sample, hbs_sample_products): HBS_PREC_FP64 needs a dense A in
- * HBS_F64 or a callback; the mixed precisions need a dense A in HBS_F32, 16-byte aligned, with
- * lda a multiple of 4 and s <= 256; HBS_PREC_FP64_TC needs a dense A in HBS_F64 (any lda >= N), s <= 256 and
- * N <= 2^20. All keep Omega, Psi, Y, Z in FP64. */
+ * HBS_F64 or a callback; HBS_PREC_MIXED_BF16X3/X6 need a dense A in HBS_F32, 16-byte aligned,
+ * with lda a multiple of 4 and s <= 256; HBS_PREC_FP64_TC and HBS_PREC_MIXED_COMPENSATED need a
+ * dense A in HBS_F64 (any lda >= N), s <= 256 and N <= 2^20. All keep Omega, Psi, Y, Z in FP64. */
 
 /* Randomized samples (Algorithm 2, first block): draws Omega (stream 0) and Psi (stream 1)
  * from `seed` as hbs_draw_gaussian does, then Y = A Omega and Z = A^* Psi.
@@ -157,11 +166,14 @@ typedef struct hbs_handle hbs_handle;   /* opaque: owns the factors and all work
  * asks for s >= max(r + m, 3r)): with L >= 1, every leaf has between r and s - r rows and
  * s >= 3r; with L = 0 (N <= leaf_max), N <= s. This build also needs s <= 192 and, for every
  * node of n rows, the sweep kernels' shared-memory tiles within 227 KB: the test block,
- * n (s + 1) + 2n doubles; the basis tile, r (n + 1) + n (r + 1) + 10 r doubles (floats in the
- * mixed precisions); in the mixed precisions the D tile, r (n + 1) + 3 n r + 3 n^2 + n floats.
- * Sweep precision: HBS_PREC_FP64 keeps every step in FP64; the mixed precisions keep the LQ of
- * each test block (nullspace and pseudo-inverse) and the sample rows pushed through it in FP64
- * and compute the bases, D_tau and the parent blocks in FP32 (factors stored in FP64).
+ * n (s + 1) + 2n doubles; the basis tile, r (n + 1) + n (r + 1) + 10 r doubles (floats with
+ * HBS_PREC_MIXED_BF16X3/X6); the reduced-precision D tile below.
+ * Sweep precision: HBS_PREC_FP64 and HBS_PREC_FP64_TC keep every step in FP64; every other
+ * precision keeps the LQ of each test block (nullspace and pseudo-inverse) and the sample rows
+ * pushed through it in FP64; HBS_PREC_MIXED_BF16X3/X6 compute the bases, D_tau and the parent
+ * blocks in FP32, HBS_PREC_MIXED_COMPENSATED the bases in FP64 and D_tau and the parent blocks
+ * in double-float (factors stored in FP64). The D and merge tiles of the reduced finishes take
+ * r (n + 1) + 3 n r + n (n + 1) + n^2 values (4-byte floats, or 8-byte pairs).
  * Errors: HBS_ERR_ARG, HBS_ERR_SHAPE, HBS_ERR_UNSUPPORTED, HBS_ERR_NOMEM, HBS_ERR_CUDA.
  */
 int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out);
@@ -218,6 +230,16 @@ int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream);
  * values to R (may be NULL); hbs_set_tuning installs saved ones (values below -8 read as -8).
  * Errors: HBS_ERR_ARG, HBS_ERR_CUDA. */
 int hbs_autotune(hbs_handle* h, void* cuda_stream);
+
+/* Measurement of the sweep (Algorithm 2, no counterpart in the paper): runs the handle's sweep
+ * once more on cuda_stream with plain launches (no graph) and CUDA events between them, and
+ * writes, per tree height t (finest first), the device times in ms of its four phases to
+ * ms[4t .. 4t+3]: the side kernel (LQ of the test blocks, sample rows), the bases, D_tau, and
+ * the merges into the parent's blocks (at most `count` values; ms may be NULL). *heights gets
+ * the number of heights. Execute the handle once first; the factors are recomputed from the
+ * same inputs. Synchronizes cuda_stream. Errors: HBS_ERR_ARG, HBS_ERR_CUDA. */
+int hbs_profile_sweep(hbs_handle* h, void* cuda_stream, float* ms, int32_t count,
+                      int32_t* heights);
 int hbs_get_tuning(const hbs_handle* h, int32_t* R, int32_t count, int32_t* heights);
 int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count);
 

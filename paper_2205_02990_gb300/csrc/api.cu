@@ -139,7 +139,20 @@ struct hbs_handle {
 
 namespace {
 
-int check_problem(const hbs_problem& p, int idx, bool fp32_nodes) {
+// The finish precision of a sweep planned with `precision`.
+int finish_of(int precision) {
+  if (precision == HBS_PREC_MIXED_BF16X3 || precision == HBS_PREC_MIXED_BF16X6) return hbs::kFinishF32;
+  if (precision == HBS_PREC_MIXED_COMPENSATED) return hbs::kFinishDF32;
+  return hbs::kFinishF64;
+}
+
+bool known_precision(int precision) {
+  return precision == HBS_PREC_FP64 || precision == HBS_PREC_MIXED_BF16X3 ||
+         precision == HBS_PREC_MIXED_BF16X6 || precision == HBS_PREC_FP64_TC ||
+         precision == HBS_PREC_MIXED_COMPENSATED;
+}
+
+int check_problem(const hbs_problem& p, int idx, int finish) {
   if (p.N < 1 || p.r < 1 || p.s < 1 || p.leaf_max < 1)
     return fail(HBS_ERR_ARG, "problem %d: N, r, s, leaf_max must be positive", idx);
   if (!p.Omega || !p.Psi || !p.Y || !p.Z)
@@ -163,7 +176,7 @@ int check_problem(const hbs_problem& p, int idx, bool fp32_nodes) {
   if (p.s > hbs::kMaxS)
     return fail(HBS_ERR_UNSUPPORTED, "problem %d: s = %d exceeds %d", idx, p.s, hbs::kMaxS);
   const int64_t nmax = (L == 0) ? p.N : std::max<int64_t>(2 * p.r, size[int64_t(1) << L]);
-  if (hbs::node_smem_bytes(int(nmax), p.r, p.s, fp32_nodes) > hbs::kMaxNodeSmemBytes)
+  if (hbs::node_smem_bytes(int(nmax), p.r, p.s, finish) > hbs::kMaxNodeSmemBytes)
     return fail(HBS_ERR_UNSUPPORTED, "problem %d: node tile of %lld x %d exceeds shared memory",
                 idx, (long long)nmax, p.s);
   return HBS_OK;
@@ -252,15 +265,14 @@ void free_handle(hbs_handle* h) {
 
 // The sweep's launches, one launch_sweep_level per height, finest height first.
 cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
-  const bool fp32_finish =
-      h->precision == HBS_PREC_MIXED_BF16X3 || h->precision == HBS_PREC_MIXED_BF16X6;
+  const int finish = finish_of(h->precision);
   // a new run: clear the abort flag an earlier run may have left (the report bits stay until
   // hbs_sync_status reads them)
   cudaError_t me = cudaMemsetAsync(h->d_status + hbs::kAbortWord, 0, sizeof(int), st);
   if (me != cudaSuccess) return me;
   for (auto& H : h->heights) {
     cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
-                                            H.max_s, fp32_finish, H.R, h->d_status, st);
+                                            H.max_s, finish, H.R, h->d_status, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -430,8 +442,7 @@ static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, 
                           const void* b, const void* c, const void* d, const char* who) {
   if (!op || !a || !b || !c || !d || s < 1 || op->N < 1)
     return fail(HBS_ERR_ARG, "%s: bad arguments", who);
-  if (precision != HBS_PREC_FP64 && precision != HBS_PREC_MIXED_BF16X3 &&
-      precision != HBS_PREC_MIXED_BF16X6 && precision != HBS_PREC_FP64_TC)
+  if (!known_precision(precision))
     return fail(HBS_ERR_ARG, "%s: unknown precision %d", who, precision);
   if (!op->A && !op->fn) return fail(HBS_ERR_ARG, "%s: operator has neither A nor fn", who);
   if (op->A && op->lda < op->N) return fail(HBS_ERR_ARG, "%s: lda < N", who);
@@ -442,7 +453,7 @@ static int check_operator(const hbs_operator* op, int32_t s, int32_t precision, 
   if (precision == HBS_PREC_FP64) {
     if (op->A && op->dtype != HBS_F64)
       return fail(HBS_ERR_UNSUPPORTED, "%s: FP64 products need a FP64 dense A", who);
-  } else if (precision == HBS_PREC_FP64_TC) {
+  } else if (precision == HBS_PREC_FP64_TC || precision == HBS_PREC_MIXED_COMPENSATED) {
     if (!op->A || op->dtype != HBS_F64)
       return fail(HBS_ERR_UNSUPPORTED, "%s: digit products need a dense FP64 A", who);
     if (s > 256 || op->N > (int64_t(1) << 20))
@@ -463,11 +474,16 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
   const int rc = check_operator(op, s, precision, Omega, Psi, Y, Z, "hbs_sample_products");
   if (rc != HBS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  if (precision == HBS_PREC_FP64_TC) {
-    static const int digits = [] {                 // 7 (default) or 6 digits per entry
+  if (precision == HBS_PREC_FP64_TC || precision == HBS_PREC_MIXED_COMPENSATED) {
+    static const int digits64 = [] {               // 7 (default) or 6 digits per entry
       const char* v = getenv("HBS_OZ_DIGITS");
       return (v && atoi(v) == 6) ? 6 : 7;
     }();
+    static const int digits_mixed = [] {           // 5 (default) or 4 digits per entry
+      const char* v = getenv("HBS_MIXED_DIGITS");
+      return (v && atoi(v) == 4) ? 4 : 5;
+    }();
+    const int digits = precision == HBS_PREC_FP64_TC ? digits64 : digits_mixed;
     cudaError_t e = hbs::launch_sample_dense_oz(static_cast<const double*>(op->A), op->lda, op->N,
                                                 Omega, Psi, s, Y, Z, digits, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core digit sampling");
@@ -531,12 +547,10 @@ int hbs_sample(const hbs_operator* op, int32_t s, uint64_t seed, int32_t precisi
 int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out) {
   if (!out || !probs || batch < 1) return fail(HBS_ERR_ARG, "hbs_plan: bad arguments");
   *out = nullptr;
-  if (precision != HBS_PREC_FP64 && precision != HBS_PREC_MIXED_BF16X3 &&
-      precision != HBS_PREC_MIXED_BF16X6 && precision != HBS_PREC_FP64_TC)
+  if (!known_precision(precision))
     return fail(HBS_ERR_UNSUPPORTED, "hbs_plan: unknown precision %d", precision);
   for (int i = 0; i < batch; ++i) {
-    const int rc = check_problem(probs[i], i, precision == HBS_PREC_MIXED_BF16X3 ||
-                                                   precision == HBS_PREC_MIXED_BF16X6);
+    const int rc = check_problem(probs[i], i, finish_of(precision));
     if (rc != HBS_OK) return rc;
   }
   auto* h = new hbs_handle();
@@ -1031,6 +1045,36 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
     cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;
   }
+  return ok();
+}
+
+int hbs_profile_sweep(hbs_handle* h, void* cuda_stream, float* ms, int32_t count,
+                      int32_t* heights) {
+  if (!h || !heights) return fail(HBS_ERR_ARG, "hbs_profile_sweep: bad arguments");
+  if (!h->tasks_uploaded) return fail(HBS_ERR_ARG, "hbs_profile_sweep: execute the handle once first");
+  if (check_device(h, "hbs_profile_sweep") != HBS_OK) return HBS_ERR_ARG;
+  *heights = int32_t(h->heights.size());
+  if (!ms) return ok();
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t ev[5];
+  int made = 0;
+  cudaError_t e = cudaSuccess;
+  for (; made < 5 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status + hbs::kAbortWord, 0, sizeof(int), st);
+  const int finish = finish_of(h->precision);
+  for (size_t t = 0; t < h->heights.size() && e == cudaSuccess; ++t) {
+    Height& H = h->heights[t];
+    e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r, H.max_s, finish,
+                                H.R, h->d_status, st, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+      float v = 0.f;
+      e = cudaEventElapsedTime(&v, ev[k], ev[k + 1]);
+      if (e == cudaSuccess && int(4 * t) + k < count) ms[4 * t + k] = v;
+    }
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return cuda_fail(e, "hbs_profile_sweep");
   return ok();
 }
 

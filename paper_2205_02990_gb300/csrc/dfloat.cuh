@@ -1,0 +1,61 @@
+// Double-float arithmetic for the compensated node products of the mixed precision: a value is
+// an unevaluated sum hi + lo of two FP32 words with |lo| <= ulp(hi) / 2, about 48 significant
+// bits in FP32's exponent range. Sums use Knuth's TwoSum and Dekker's Fast2Sum, products the
+// exact FMA residual of hi * hi (Dekker 1971; Joldes, Muller and Popescu, ACM TOMS 2017, the
+// "sloppy" variants). Every operation runs on the FP32 pipe, which GB300 drives at 64 times the
+// FP64 rate; all roundings are explicit (__fadd_rn etc.), so the compiler can neither contract
+// nor reorder them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hbs {
+
+struct dfloat {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {   // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// The double-float nearest to an FP64 value (to ~2^-48 relative; FP32 exponent range).
+__device__ __forceinline__ dfloat df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - static_cast<double>(h))};
+}
+
+__device__ __forceinline__ double df_to(dfloat a) {
+  return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+
+// a * b + c
+__device__ __forceinline__ dfloat df_fma(dfloat a, dfloat b, dfloat c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);                 // exact: a.hi b.hi = p + e
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const dfloat s = df_two_sum(c.hi, p);
+  const float t = __fadd_rn(s.lo, __fadd_rn(c.lo, e));
+  return df_fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const dfloat s = df_two_sum(a.hi, b.hi);
+  const float t = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return df_fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ dfloat df_zero() { return {0.f, 0.f}; }
+
+}  // namespace hbs

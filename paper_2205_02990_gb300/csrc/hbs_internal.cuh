@@ -73,16 +73,19 @@ cudaError_t launch_build_apply_tasks(const ApplyNode* nodes, int L, int r, int64
 
 // Shared memory of the sweep kernels for a node of n rows (sweep.cu).
 size_t side_smem_doubles(int n, int s);
-size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes);   // largest sweep-kernel tile
+// The finish of a sweep (bases, D_tau, merges): FP64, FP32, or double-float (FP32 pairs).
+constexpr int kFinishF64 = 0, kFinishF32 = 1, kFinishDF32 = 2;
+size_t node_smem_bytes(int n, int r, int s, int finish);   // largest sweep-kernel tile
 constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
 constexpr int kMaxSideCluster = 8;      // CTAs sharing one test-block factorization
 
 // One tree height of Algorithm 2: the side kernel (FP64), then the bases, D_tau and merge
-// kernels (FP64, or FP32 when fp32_finish).
+// kernels in the given finish precision. With marks (5 events), records them before the side
+// kernel and after the side, bases, D and merge launches.
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
-                               int max_s, bool fp32_finish, int row_splits, int* d_status,
-                               cudaStream_t st);
+                               int max_s, int finish, int row_splits, int* d_status,
+                               cudaStream_t st, cudaEvent_t* marks = nullptr);
 // The side kernel of one height alone (for tuning; idempotent). R > 0: R row slices per
 // (node, side), each CTA factoring the test block; R < 0: a cluster of -R CTAs per (node, side)
 // sharing one factorization.
@@ -114,7 +117,7 @@ cudaError_t sample_tc_inject(int bits);
 // wider s as tiles of 128 (sample_tc.cu).
 void column_tiles(int s, int* BN, int* BNt);
 // FP64-class sampling by exact bfloat16 digit products on the tensor cores (sample_oz.cu):
-// A FP64 row-major (any lda >= N), digits = 6 or 7, s <= 256, N <= 2^20. The scratch it grows
+// A FP64 row-major (any lda >= N), digits = 4 .. 7, s <= 256, N <= 2^20. The scratch it grows
 // holds the device status word at its start.
 cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, const double* Om,
                                    const double* Ps, int s, double* Y, double* Z, int digits,

@@ -21,9 +21,11 @@
 //
 // Finish kernels, per level after the side kernel: node_bases (col(., r): an unpivoted
 // Householder QR whose first r columns are formed by backward accumulation; FP64, or FP32 in the
-// mixed precisions), then D_tau from D = WY + U (Q - P - R V^*) (node_dblk_a / node_dblk_b in
-// FP64, over column blocks; node_dchain_f32 in FP32, which also forms U^* D and (D V)^*), then
-// the parent's blocks (node_merge / node_merge_f32, over column chunks).
+// plain mixed finish), then D_tau from D = WY + U (Q - P - R V^*) (node_dblk_a / node_dblk_b in
+// FP64, over column blocks; node_dchain in FP32 or in double-float, which also forms U^* D and
+// (D V)^*), then the parent's blocks (node_merge in FP64 / node_merge_r in FP32 or double-float,
+// over column chunks). The double-float finish (compensated FP32 pairs, dfloat.cuh) keeps ~48
+// bits on the FP32 pipe.
 //
 // Reflectors use LAPACK's sign choice (beta = -sign(alpha) ||x||; identity when the tail is
 // zero) and are stored with their leading 1 explicit. Mapping: 256 threads = 32 groups of 8
@@ -34,6 +36,7 @@
 
 #include <cooperative_groups.h>
 
+#include "dfloat.cuh"
 #include "hbs_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -629,25 +632,38 @@ __global__ void __launch_bounds__(THREADS)
   }
 }
 
-// Small FP32 product in shared memory with a register tile per thread: for i < M, j < N,
+// Arithmetic of the reduced-precision finish kernels: Real = float (plain FP32, the "mixed"
+// finish) or dfloat (double-float, the compensated finish). Loads convert once from FP64, stores
+// convert back.
+__device__ __forceinline__ float nfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ dfloat nfma(dfloat a, dfloat b, dfloat c) { return df_fma(a, b, c); }
+__device__ __forceinline__ float nneg(float a) { return -a; }
+__device__ __forceinline__ dfloat nneg(dfloat a) { return df_neg(a); }
+template <class Real> __device__ __forceinline__ Real from_f64(double x);
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return static_cast<float>(x); }
+template <> __device__ __forceinline__ dfloat from_f64<dfloat>(double x) { return df_from(x); }
+__device__ __forceinline__ double to_f64(float v) { return static_cast<double>(v); }
+__device__ __forceinline__ double to_f64(dfloat v) { return df_to(v); }
+
+// Small product in shared memory with a register tile per thread: for i < M, j < N,
 // C(i, j) = init(i, j) + sum_k a(i, k) b(k, j), stored by out(i, j, value). A warp takes a tile
 // of TM rows and 32 TN columns, lane l the columns l, l + 32, ...: a(i, k) is the same for the
 // whole warp (one broadcast) and b(k, j) is read by consecutive lanes (no bank conflicts), so
 // each k costs TM + TN shared loads per warp for 32 TM TN multiply-adds.
-template <int TM, int TN, class FA, class FB, class FI, class FO>
+template <class Real, int TM, int TN, class FA, class FB, class FI, class FO>
 __device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI init, FO out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tn = (N + 32 * TN - 1) / (32 * TN), tm = (M + TM - 1) / TM;
   for (int t = warp; t < tm * tn; t += THREADS / 32) {
     const int i0 = (t / tn) * TM, j0 = (t % tn) * 32 * TN + lane;
-    float acc[TM][TN];
+    Real acc[TM][TN];
 #pragma unroll
     for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
       for (int jj = 0; jj < TN; ++jj)
-        acc[ii][jj] = (i0 + ii < M && j0 + 32 * jj < N) ? init(i0 + ii, j0 + 32 * jj) : 0.f;
+        acc[ii][jj] = (i0 + ii < M && j0 + 32 * jj < N) ? init(i0 + ii, j0 + 32 * jj) : Real{};
     for (int k = 0; k < K; ++k) {
-      float av[TM], bv[TN];
+      Real av[TM], bv[TN];
 #pragma unroll
       for (int ii = 0; ii < TM; ++ii) av[ii] = a(min(i0 + ii, M - 1), k);
 #pragma unroll
@@ -655,7 +671,7 @@ __device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI in
 #pragma unroll
       for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fmaf(av[ii], bv[jj], acc[ii][jj]);
+        for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = nfma(av[ii], bv[jj], acc[ii][jj]);
     }
 #pragma unroll
     for (int ii = 0; ii < TM; ++ii)
@@ -665,82 +681,102 @@ __device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI in
   }
 }
 
-// FP32 D products with every operand staged in shared memory once. On GB300 a conversion from
-// FP64 runs at the FP64 rate, so converting each operand inside the product loops (one
-// conversion per FMA) would make this kernel as slow as FP64 arithmetic; staged, a node converts
-// each input entry once. One CTA per node, after node_bases<float> has written U and V: D_tau
-// (stored as FP64), then U^* D and (D V)^* (r x n) into the spent XY and XZ for node_merge_f32.
+// D products with every operand staged in shared memory once. On GB300 a conversion from FP64
+// runs at the FP64 rate, so converting each operand inside the product loops (one conversion
+// per multiply-add) would make this kernel as slow as FP64 arithmetic; staged, a node converts
+// each input entry once. One CTA per node, after node_bases has written U and V: D_tau (stored as
+// FP64), then U^* D and (D V)^* (r x n) into the spent XY and XZ for node_merge_r. Real = float
+// stores those as FP64; Real = dfloat stores them, and U and V, as double-float pairs (two
+// floats in each 8-byte slot: U^* D and (D V)^* in XY, XZ; U, V in the spent WY, WZ), so that
+// node_merge_r<dfloat> reads them without converting again.
+template <class Real>
 __global__ void __launch_bounds__(THREADS, 1)
-    node_dchain_f32(const NodeTask* __restrict__ tasks) {
-  extern __shared__ __align__(16) float fsm[];
+    node_dchain(const NodeTask* __restrict__ tasks) {
+  extern __shared__ __align__(16) unsigned char dch_bytes[];
+  Real* fsm = reinterpret_cast<Real*>(dch_bytes);
   const NodeTask tk = tasks[blockIdx.x];
   if (tk.is_root) return;
   const int n = tk.n, r = tk.r;
   const int ldX = n + 1, ldT = n + 1;
-  float* G1 = fsm;                                     // r x ldX: V^* WZ, later U^* D
-  float* Hs = G1 + static_cast<size_t>(r) * ldX;       // r x n: U^*(T2^* - WY), later (D V)^*
-  float* Us = Hs + static_cast<size_t>(r) * n;         // n x r
-  float* Vs = Us + static_cast<size_t>(n) * r;         // n x r
-  float* T2 = Vs + static_cast<size_t>(n) * r;         // n x ldT: (I - VV^*) WZ, later D
-  float* WYs = T2 + static_cast<size_t>(n) * ldT;      // n x n
-  float* WZs = WYs + static_cast<size_t>(n) * n;       // n x n
+  Real* G1 = fsm;                                      // r x ldX: V^* WZ, later U^* D
+  Real* Hs = G1 + static_cast<size_t>(r) * ldX;        // r x n: U^*(T2^* - WY), later (D V)^*
+  Real* Us = Hs + static_cast<size_t>(r) * n;          // n x r
+  Real* Vs = Us + static_cast<size_t>(n) * r;          // n x r
+  Real* T2 = Vs + static_cast<size_t>(n) * r;          // n x ldT: WZ, then (I - VV^*) WZ, then D
+  Real* WYs = T2 + static_cast<size_t>(n) * ldT;       // n x n
   for (int e = threadIdx.x; e < n * r; e += THREADS) {
-    Us[e] = static_cast<float>(tk.U[e]);
-    Vs[e] = static_cast<float>(tk.V[e]);
+    Us[e] = from_f64<Real>(tk.U[e]);
+    Vs[e] = from_f64<Real>(tk.V[e]);
   }
   for (int e = threadIdx.x; e < n * n; e += THREADS) {
-    WYs[e] = static_cast<float>(tk.WY[e]);
-    WZs[e] = static_cast<float>(tk.WZ[e]);
+    WYs[e] = from_f64<Real>(tk.WY[e]);
+    T2[(e / n) * ldT + e % n] = from_f64<Real>(tk.WZ[e]);
   }
   __syncthreads();
   // G1 = V^* WZ (r x n)
-  tile_gemm<4, 1>(r, n, n, [&](int c, int i) { return Vs[i * r + c]; },
-                  [&](int i, int j) { return WZs[i * n + j]; }, [](int, int) { return 0.f; },
-                  [&](int c, int j, float v) { G1[c * ldX + j] = v; });
+  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int i) { return Vs[i * r + c]; },
+                        [&](int i, int j) { return T2[i * ldT + j]; }, [](int, int) { return Real{}; },
+                        [&](int c, int j, Real v) { G1[c * ldX + j] = v; });
   __syncthreads();
-  // T2 = WZ - V G1 (n x n)
-  tile_gemm<8, 1>(n, n, r, [&](int i, int c) { return -Vs[i * r + c]; },
-                  [&](int c, int j) { return G1[c * ldX + j]; },
-                  [&](int i, int j) { return WZs[i * n + j]; },
-                  [&](int i, int j, float v) { T2[i * ldT + j] = v; });
+  // T2 = WZ - V G1 (n x n), in place: each entry reads only its own WZ value
+  tile_gemm<Real, 8, 1>(n, n, r, [&](int i, int c) { return nneg(Vs[i * r + c]); },
+                        [&](int c, int j) { return G1[c * ldX + j]; },
+                        [&](int i, int j) { return T2[i * ldT + j]; },
+                        [&](int i, int j, Real v) { T2[i * ldT + j] = v; });
   __syncthreads();
   // G1 = U^* T2^* (= U^* D), then Hs = G1 - U^* WY
-  tile_gemm<4, 1>(r, n, n, [&](int c, int i) { return Us[i * r + c]; },
-                  [&](int i, int j) { return T2[j * ldT + i]; }, [](int, int) { return 0.f; },
-                  [&](int c, int j, float v) { G1[c * ldX + j] = v; });
+  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int i) { return Us[i * r + c]; },
+                        [&](int i, int j) { return T2[j * ldT + i]; }, [](int, int) { return Real{}; },
+                        [&](int c, int j, Real v) { G1[c * ldX + j] = v; });
   __syncthreads();
-  tile_gemm<4, 1>(r, n, n, [&](int c, int i) { return -Us[i * r + c]; },
-                  [&](int i, int j) { return WYs[i * n + j]; },
-                  [&](int c, int j) { return G1[c * ldX + j]; },
-                  [&](int c, int j, float v) { Hs[c * n + j] = v; });
+  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int i) { return nneg(Us[i * r + c]); },
+                        [&](int i, int j) { return WYs[i * n + j]; },
+                        [&](int c, int j) { return G1[c * ldX + j]; },
+                        [&](int c, int j, Real v) { Hs[c * n + j] = v; });
   __syncthreads();
   // D = WY + U Hs (n x n), stored as FP64 and kept in T2
-  tile_gemm<8, 1>(n, n, r, [&](int i, int c) { return Us[i * r + c]; },
-                  [&](int c, int j) { return Hs[c * n + j]; },
-                  [&](int i, int j) { return WYs[i * n + j]; },
-                  [&](int i, int j, float v) {
-                    tk.D[static_cast<size_t>(i) * n + j] = static_cast<double>(v);
-                    T2[i * ldT + j] = v;
-                  });
+  tile_gemm<Real, 8, 1>(n, n, r, [&](int i, int c) { return Us[i * r + c]; },
+                        [&](int c, int j) { return Hs[c * n + j]; },
+                        [&](int i, int j) { return WYs[i * n + j]; },
+                        [&](int i, int j, Real v) {
+                          tk.D[static_cast<size_t>(i) * n + j] = to_f64(v);
+                          T2[i * ldT + j] = v;
+                        });
   __syncthreads();
   // Hs = (D V)^* (r x n)
-  tile_gemm<4, 1>(r, n, n, [&](int c, int j) { return Vs[j * r + c]; },
-                  [&](int j, int i) { return T2[i * ldT + j]; }, [](int, int) { return 0.f; },
-                  [&](int c, int i, float v) { Hs[c * n + i] = v; });
+  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int j) { return Vs[j * r + c]; },
+                        [&](int j, int i) { return T2[i * ldT + j]; }, [](int, int) { return Real{}; },
+                        [&](int c, int i, Real v) { Hs[c * n + i] = v; });
   __syncthreads();
-  for (int e = threadIdx.x; e < r * n; e += THREADS) {
-    const int c = e / n, i = e % n;
-    tk.XY[e] = static_cast<double>(G1[c * ldX + i]);
-    tk.XZ[e] = static_cast<double>(Hs[e]);
+  if constexpr (sizeof(Real) == sizeof(double)) {
+    Real* XYd = reinterpret_cast<Real*>(tk.XY);
+    Real* XZd = reinterpret_cast<Real*>(tk.XZ);
+    Real* Ud = reinterpret_cast<Real*>(tk.WY);
+    Real* Vd = reinterpret_cast<Real*>(tk.WZ);
+    for (int e = threadIdx.x; e < r * n; e += THREADS) {
+      const int c = e / n, i = e % n;
+      XYd[e] = G1[c * ldX + i];
+      XZd[e] = Hs[e];
+      Ud[e] = Us[e];
+      Vd[e] = Vs[e];
+    }
+  } else {
+    for (int e = threadIdx.x; e < r * n; e += THREADS) {
+      const int c = e / n, i = e % n;
+      tk.XY[e] = to_f64(G1[c * ldX + i]);
+      tk.XZ[e] = to_f64(Hs[e]);
+    }
   }
 }
 
-// FP32 merges (Eq. omega_tau_and_y_tau): grid (node, chunk of kw columns, pass) as node_merge,
-// from U, V and the products U^* D, (D V)^* that node_dchain_f32 left in XY, XZ; the chunk, the
-// bases and the product are staged in shared memory as FP32.
+// Merges (Eq. omega_tau_and_y_tau): grid (node, chunk of kw columns, pass) as node_merge, from U,
+// V and the products U^* D, (D V)^* that node_dchain left behind; the chunk, the bases and the
+// product are staged in shared memory.
+template <class Real>
 __global__ void __launch_bounds__(THREADS)
-    node_merge_f32(const NodeTask* __restrict__ tasks, int chunk) {
-  extern __shared__ __align__(16) float msf[];
+    node_merge_r(const NodeTask* __restrict__ tasks, int chunk) {
+  extern __shared__ __align__(16) unsigned char mr_bytes[];
+  Real* msf = reinterpret_cast<Real*>(mr_bytes);
   const NodeTask tk = tasks[blockIdx.x];
   if (tk.is_root) return;
   const int n = tk.n, r = tk.r, s = tk.s;
@@ -750,36 +786,49 @@ __global__ void __launch_bounds__(THREADS)
   const int pass = blockIdx.z;
   const double* T = pass ? tk.Ps : tk.Om;
   const double* S = pass ? tk.Z : tk.Y;
-  const double* Bt = pass ? tk.U : tk.V;               // reduces the test block
-  const double* Bs = pass ? tk.V : tk.U;               // reduces the sample block
-  const double* H = pass ? tk.XZ : tk.XY;              // (D V)^* or U^* D, r x n
   double* outT = pass ? tk.Ps_p : tk.Om_p;
   double* outS = pass ? tk.Z_p : tk.Y_p;
-  float* Ts = msf;                                     // n x kw
-  float* Ss = Ts + static_cast<size_t>(n) * kw;        // n x kw
-  float* Bts = Ss + static_cast<size_t>(n) * kw;       // n x r
-  float* Bss = Bts + static_cast<size_t>(n) * r;       // n x r
-  float* Hsm = Bss + static_cast<size_t>(n) * r;       // r x n
+  Real* Ts = msf;                                      // n x kw
+  Real* Ss = Ts + static_cast<size_t>(n) * kw;         // n x kw
+  Real* Bts = Ss + static_cast<size_t>(n) * kw;        // n x r: reduces the test block
+  Real* Bss = Bts + static_cast<size_t>(n) * r;        // n x r: reduces the sample block
+  Real* Hsm = Bss + static_cast<size_t>(n) * r;        // r x n: (D V)^* or U^* D
   for (int e = threadIdx.x; e < n * kw; e += THREADS) {
     const int i = e / kw, k = e % kw;
-    Ts[e] = static_cast<float>(T[static_cast<size_t>(i) * s + k0 + k]);
-    Ss[e] = static_cast<float>(S[static_cast<size_t>(i) * s + k0 + k]);
+    Ts[e] = from_f64<Real>(T[static_cast<size_t>(i) * s + k0 + k]);
+    Ss[e] = from_f64<Real>(S[static_cast<size_t>(i) * s + k0 + k]);
   }
-  for (int e = threadIdx.x; e < n * r; e += THREADS) {
-    Bts[e] = static_cast<float>(Bt[e]);
-    Bss[e] = static_cast<float>(Bs[e]);
-    Hsm[e] = static_cast<float>(H[e]);
+  if constexpr (sizeof(Real) == sizeof(double)) {      // left as pairs by node_dchain
+    const Real* Ud = reinterpret_cast<const Real*>(tk.WY);
+    const Real* Vd = reinterpret_cast<const Real*>(tk.WZ);
+    const Real* H = reinterpret_cast<const Real*>(pass ? tk.XZ : tk.XY);
+    const Real* Bt = pass ? Ud : Vd;
+    const Real* Bs = pass ? Vd : Ud;
+    for (int e = threadIdx.x; e < n * r; e += THREADS) {
+      Bts[e] = Bt[e];
+      Bss[e] = Bs[e];
+      Hsm[e] = H[e];
+    }
+  } else {
+    const double* Bt = pass ? tk.U : tk.V;
+    const double* Bs = pass ? tk.V : tk.U;
+    const double* H = pass ? tk.XZ : tk.XY;
+    for (int e = threadIdx.x; e < n * r; e += THREADS) {
+      Bts[e] = from_f64<Real>(Bt[e]);
+      Bss[e] = from_f64<Real>(Bs[e]);
+      Hsm[e] = from_f64<Real>(H[e]);
+    }
   }
   __syncthreads();
-  tile_gemm<2, 1>(r, kw, n, [&](int c, int i) { return Bts[i * r + c]; },
-                  [&](int i, int k) { return Ts[i * kw + k]; }, [](int, int) { return 0.f; },
-                  [&](int c, int k, float v) { outT[c * s + k0 + k] = static_cast<double>(v); });
+  tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return Bts[i * r + c]; },
+                        [&](int i, int k) { return Ts[i * kw + k]; }, [](int, int) { return Real{}; },
+                        [&](int c, int k, Real v) { outT[c * s + k0 + k] = to_f64(v); });
   // U^* S - H T as one product over 2n: [Bs^*, -H] [S; T]
-  tile_gemm<2, 1>(r, kw, 2 * n,
-                  [&](int c, int i) { return i < n ? Bss[i * r + c] : -Hsm[c * n + i - n]; },
-                  [&](int i, int k) { return i < n ? Ss[i * kw + k] : Ts[(i - n) * kw + k]; },
-                  [](int, int) { return 0.f; },
-                  [&](int c, int k, float v) { outS[c * s + k0 + k] = static_cast<double>(v); });
+  tile_gemm<Real, 2, 1>(r, kw, 2 * n,
+                        [&](int c, int i) { return i < n ? Bss[i * r + c] : nneg(Hsm[c * n + i - n]); },
+                        [&](int i, int k) { return i < n ? Ss[i * kw + k] : Ts[(i - n) * kw + k]; },
+                        [](int, int) { return Real{}; },
+                        [&](int c, int k, Real v) { outS[c * s + k0 + k] = to_f64(v); });
 }
 
 template <class Kernel>
@@ -807,23 +856,25 @@ size_t dblk_smem_doubles(int r, int nb) {
 // re-forms the r x r product R, r^2 n flops, against ~4 r n^2 / blocks of its own work).
 int dblk_blocks(int ntasks) { return std::max(1, std::min(8, (2 * 152) / std::max(1, ntasks))); }
 
-// FP32 D products: G1, Hs, T2 and the staged U, V, WY, WZ (floats).
-size_t dchain_f32_smem_floats(int n, int r) {
+// Reduced-precision D products (node_dchain): G1, Hs, the staged U, V, T2 (which holds WZ) and
+// WY, in units of the kernel's Real.
+size_t dchain_smem_reals(int n, int r) {
   return static_cast<size_t>(r) * (n + 1) + static_cast<size_t>(r) * n +
          2 * static_cast<size_t>(n) * r + static_cast<size_t>(n) * (n + 1) +
-         2 * static_cast<size_t>(n) * n;
+         static_cast<size_t>(n) * n;
 }
-size_t merge_f32_smem_floats(int n, int r, int chunk) {
+size_t merge_r_smem_reals(int n, int r, int chunk) {
   return 2 * static_cast<size_t>(n) * chunk + 3 * static_cast<size_t>(n) * r;
 }
 
 // The largest shared-memory tile the sweep kernels need for a node of n rows.
-size_t node_smem_bytes(int n, int r, int s, bool fp32_nodes) {
-  const size_t d = sizeof(double), f = sizeof(float);
+size_t node_smem_bytes(int n, int r, int s, int finish) {
+  const size_t d = sizeof(double);
   const size_t common = std::max(side_smem_doubles(n, s) * d, bases_smem_doubles(n, r) * d);
-  if (fp32_nodes)
-    return std::max({common, dchain_f32_smem_floats(n, r) * f,
-                     merge_f32_smem_floats(n, r, kMergeCols) * f});
+  if (finish == kFinishF32 || finish == kFinishDF32) {
+    const size_t w = finish == kFinishF32 ? sizeof(float) : sizeof(dfloat);
+    return std::max({common, dchain_smem_reals(n, r) * w, merge_r_smem_reals(n, r, kMergeCols) * w});
+  }
   return std::max({common, dblk_smem_doubles(r, n) * d, merge_smem_doubles(n) * d});
 }
 
@@ -912,29 +963,37 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
 }
 
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
-                               int max_s, bool fp32_finish, int row_splits, int* d_status,
-                               cudaStream_t st) {
+                               int max_s, int finish, int row_splits, int* d_status,
+                               cudaStream_t st, cudaEvent_t* marks) {
   if (ntasks <= 0) return cudaSuccess;
+  auto mark = [&](int i) { return marks ? cudaEventRecord(marks[i], st) : cudaSuccess; };
   if (max_s > kMaxS) return cudaErrorInvalidValue;
+  const bool reduced = finish == kFinishF32 || finish == kFinishDF32;
+  const size_t rsize = finish == kFinishF32 ? sizeof(float) : sizeof(dfloat);
   // about four merge CTAs per SM in all; chunks of 8 .. 32 columns
   const int want = std::max(1, (4 * 152) / (2 * ntasks));
   const int chunk = std::max(8, std::min(kMergeCols, (max_s + want - 1) / want));
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
   const size_t bases_bytes = bases_smem_doubles(max_n, max_r) *
-                             (fp32_finish ? sizeof(float) : sizeof(double));
+                             (finish == kFinishF32 ? sizeof(float) : sizeof(double));
   const int blocks = dblk_blocks(ntasks);
   const int nb = (max_n + blocks - 1) / blocks;
-  const size_t dblk_bytes = fp32_finish ? dchain_f32_smem_floats(max_n, max_r) * sizeof(float)
-                                        : dblk_smem_doubles(max_r, nb) * sizeof(double);
-  const size_t merge_bytes = fp32_finish ? merge_f32_smem_floats(max_n, max_r, chunk) * sizeof(float)
-                                         : merge_smem_doubles(max_n) * sizeof(double);
+  const size_t dblk_bytes = reduced ? dchain_smem_reals(max_n, max_r) * rsize
+                                    : dblk_smem_doubles(max_r, nb) * sizeof(double);
+  const size_t merge_bytes = reduced ? merge_r_smem_reals(max_n, max_r, chunk) * rsize
+                                     : merge_smem_doubles(max_n) * sizeof(double);
   if (side_bytes > kMaxNodeSmemBytes || bases_bytes > kMaxNodeSmemBytes ||
       dblk_bytes > kMaxNodeSmemBytes || merge_bytes > kMaxNodeSmemBytes)
     return cudaErrorInvalidValue;
-  cudaError_t e = launch_side_only(d_tasks, ntasks, max_n, max_s,
-                       row_splits != 0 ? row_splits : side_row_splits(ntasks, max_n, max_s), d_status, st);
+  cudaError_t e = mark(0);
+  if (e == cudaSuccess)
+    e = launch_side_only(d_tasks, ntasks, max_n, max_s,
+                         row_splits != 0 ? row_splits : side_row_splits(ntasks, max_n, max_s),
+                         d_status, st);
+  if (e == cudaSuccess) e = mark(1);
   if (e != cudaSuccess) return e;
   // bases: one CTA per (node, side); the register slots span the n <= s columns of a basis
+  // (FP32 in the plain mixed finish; FP64 otherwise, the double-float finish included)
   const dim3 bgrid(static_cast<unsigned>(ntasks), 2u);
   auto bases = [&](auto kernel) {
     e = allow_smem(kernel);
@@ -943,24 +1002,32 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
       e = cudaGetLastError();
     }
   };
-  if (fp32_finish) {
+  if (finish == kFinishF32) {
     bases(node_bases<float>);
   } else {
     bases(node_bases<double>);
   }
+  if (e == cudaSuccess) e = mark(2);
   if (e != cudaSuccess) return e;
   const dim3 merge_grid(static_cast<unsigned>(ntasks),
                         static_cast<unsigned>((max_s + chunk - 1) / chunk), 2u);
-  if (fp32_finish) {
-    e = allow_smem(node_dchain_f32);
-    if (e != cudaSuccess) return e;
-    node_dchain_f32<<<ntasks, THREADS, dblk_bytes, st>>>(d_tasks);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = allow_smem(node_merge_f32);
-    if (e != cudaSuccess) return e;
-    node_merge_f32<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
-    return cudaGetLastError();
+  if (reduced) {
+    auto finish_pair = [&](auto dchain, auto merge) {
+      e = allow_smem(dchain);
+      if (e != cudaSuccess) return;
+      dchain<<<ntasks, THREADS, dblk_bytes, st>>>(d_tasks);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = mark(3);
+      if (e != cudaSuccess) return;
+      e = allow_smem(merge);
+      if (e != cudaSuccess) return;
+      merge<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = mark(4);
+    };
+    if (finish == kFinishF32) finish_pair(node_dchain<float>, node_merge_r<float>);
+    else finish_pair(node_dchain<dfloat>, node_merge_r<dfloat>);
+    return e;
   }
   const dim3 dgrid(static_cast<unsigned>(ntasks), static_cast<unsigned>(blocks));
   node_dblk_a<<<dgrid, THREADS, 0, st>>>(d_tasks, nb);
@@ -970,11 +1037,14 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   if (e != cudaSuccess) return e;
   node_dblk_b<<<dgrid, THREADS, dblk_bytes, st>>>(d_tasks, nb);
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = mark(3);
   if (e != cudaSuccess) return e;
   e = allow_smem(node_merge);
   if (e != cudaSuccess) return e;
   node_merge<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = mark(4);
+  return e;
 }
 
 }  // namespace hbs

@@ -28,6 +28,7 @@ HBS_PREC_FP64 = 0
 HBS_PREC_MIXED_BF16X3 = 1
 HBS_PREC_MIXED_BF16X6 = 2
 HBS_PREC_FP64_TC = 3
+HBS_PREC_MIXED_COMPENSATED = 4
 HBS_F64 = 0
 HBS_F32 = 1
 
@@ -36,7 +37,7 @@ EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan"
             "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
             "hbs_apply_static", "hbs_sample_sync", "hbs_apply_batch", "hbs_load_factors",
             "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph",
-            "hbs_test_inject_status", "hbs_probe_peaks"]
+            "hbs_test_inject_status", "hbs_probe_peaks", "hbs_profile_sweep"]
 
 
 class HBSError(RuntimeError):
@@ -95,6 +96,8 @@ def load():
         "hbs_sync_status": (c.c_int, [c.c_void_p, c.c_void_p]),
         "hbs_test_inject_status": (c.c_int, [c.c_void_p, c.c_int32]),
         "hbs_probe_peaks": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_double), c.c_void_p]),
+        "hbs_profile_sweep": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int32,
+                                        c.POINTER(c.c_int32)]),
         "hbs_free": (None, [c.c_void_p]),
         "hbs_last_error": (c.c_char_p, []),
         "hbs_tree": (c.c_int, [c.c_void_p, c.c_int32, c.POINTER(c.c_int32), c.c_void_p, c.c_void_p]),
@@ -320,6 +323,17 @@ def hbs_autotune(handle):
     """Time the side kernel's shapes (row slices R > 0, clusters R = -C) per tree height on the
     current inputs; keep the best."""
     _check(load().hbs_autotune(handle.ptr, _stream()))
+
+
+def hbs_profile_sweep(handle):
+    """Per tree height (finest first): device ms of the side, bases, D and merge phases of one
+    more sweep with plain launches."""
+    lib = load()
+    n = ctypes.c_int32()
+    _check(lib.hbs_profile_sweep(handle.ptr, _stream(), None, 0, ctypes.byref(n)))
+    ms = (ctypes.c_float * max(4 * n.value, 1))()
+    _check(lib.hbs_profile_sweep(handle.ptr, _stream(), ms, 4 * n.value, ctypes.byref(n)))
+    return [list(ms[4 * t:4 * t + 4]) for t in range(n.value)]
 
 
 def hbs_get_tuning(handle):

@@ -297,3 +297,27 @@ def test_double_layer_accuracy_matches_oracle(hb):
     e_gpu, e_orc = rel(At, A), rel(Ao, A)
     assert e_gpu <= 1e-6 and e_orc <= 1e-6
     assert e_gpu <= 3 * e_orc and e_orc <= 3 * e_gpu
+
+
+def test_profile_sweep_times_every_phase_and_keeps_factors(hb):
+    # hbs_profile_sweep re-runs the sweep with plain launches and events between them: one
+    # time per (height, phase), and the factors it leaves are bit-identical (same inputs)
+    N, r, s, leaf = 2048, 40, 120, 64
+    x = [dev(gaussian((N, s), 40 + i)) for i in range(4)]
+    h = hb.hbs_compress([hb.Problem(N, r, s, leaf, *x)])
+    hb.hbs_sync_status(h)
+    L = hb.hbs_tree(h)[0]
+    before = [hb.hbs_get_node(h, t) for t in range(1, 2 ** (L + 1))]
+    ms = hb.hbs_profile_sweep(h)
+    hb.hbs_sync_status(h)
+    assert len(ms) == L + 1
+    for t, row in enumerate(ms):
+        assert len(row) == 4 and all(v >= 0 for v in row)
+        assert row[0] > 0                                  # every height runs the side kernel
+        if t < L:
+            assert min(row) > 0                            # and, below the root, all four
+    after = [hb.hbs_get_node(h, t) for t in range(1, 2 ** (L + 1))]
+    for a, b in zip(before, after):
+        for u, v in zip(a, b):
+            assert (u is None and v is None) or torch.equal(u, v)
+    h.free()
