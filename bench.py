@@ -104,6 +104,12 @@ def merge_flops(n, r, s, reduced):
     return 12 * n * r * s if reduced else 4 * n * n * s + 8 * n * r * s
 
 
+def sweep_launches(N, r, s, leaf, tuning, reduced):
+    """Kernel launches of one sweep: per height the side, bases, D (two kernels in FP64) and
+    merge kernels (the root height runs all of them too)."""
+    return len(tuning) * ((1 + 3) if reduced else (1 + 4))
+
+
 def sweep_phase_flops(N, r, s, leaf, reduced):
     """Per height (finest first): flops of the side, bases, D and merge phases."""
     L = tree_nodes(N, leaf)
@@ -777,7 +783,11 @@ def main():
         elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3)
         per_launch = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * steps)
         phases = hb.hbs_profile_sweep(h)                   # one more sweep, events per launch
-        return dict(h=h, step=step, elapsed=elapsed, per_launch=per_launch,
+
+        def products_ms():                                 # of the steps timed with events
+            return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+        return dict(h=h, step=step, elapsed=elapsed, per_launch=per_launch, products_ms=products_ms,
                     clocks=clk.summary() if clk else None, tuning=hb.hbs_get_tuning(h),
                     sweep=sweep_roofline(phases, N, r, s, leaf, FINISH[cfg["sweep"]], peaks))
 
@@ -829,20 +839,20 @@ def main():
         dst = src                                   # the device copy the step multiplies
         streamed = cfg["sample"] == 0               # FP64 products take the pinned A directly
 
-        def e2e_step():
+        def e2e_step(k=None):
             if streamed:                            # row blocks copied under the products
-                res["step"](A_src=A_host)
+                res["step"](k, A_src=A_host)
             else:
                 dst.copy_(A_host, non_blocking=True)
-                res["step"]()
+                res["step"](k)
             hb.hbs_copy_factors(h, F_host)
 
         e2e_step()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        for k in range(args.steps):
+            e2e_step(k)
         e1.record(stream)
         barrier()
         te = max_over_ranks(e0.elapsed_time(e1) / 1e3)
@@ -855,6 +865,7 @@ def main():
         c[2].record(stream)
         barrier()
         h2d_ms, d2h_ms = c[0].elapsed_time(c[1]), c[1].elapsed_time(c[2])
+        streamed_products_ms = res["products_ms"]()          # both products, per e2e step
         a_bytes = src.numel() * src.element_size()
         e2e_ms = te / args.steps * 1e3
         dev_ms = res["elapsed"] / args.steps * 1e3
@@ -862,6 +873,8 @@ def main():
                "ms_per_step": e2e_ms, "device_ms_per_step": dev_ms,
                "overhead_ms_per_step": e2e_ms - dev_ms,
                "h2d_ms_all_of_A": h2d_ms, "h2d_gbs": a_bytes / h2d_ms / 1e6,
+               "products_ms_per_step": streamed_products_ms,
+               "products_ms_per_step_device_A": 2 * res["per_launch"] * 1e3,
                "d2h_ms_factors": d2h_ms, "d2h_gbs": hb.hbs_factor_bytes(h) / d2h_ms / 1e6,
                "host": {k: (len(v) if isinstance(v, list) else v) for k, v in host_info.items()},
                "a_transfer": "A streamed from pinned host memory by the library, copies overlapping "
@@ -921,7 +934,8 @@ def main():
         # kernels; FP32: one)
         "gpu_launches": args.steps * ({0: 2 + 2 + 2, 1: 2 + 6, 2: 2 + 6, 3: 2 + 3 + 4,
                                        4: 2 + 3 + 4}[MODES[head]["sample"]]
-                                      + (4 if MODES[head]["sweep"] in (1, 2, 4) else 5) * (L + 1)),
+                                      + sweep_launches(N, r, s, leaf, res["tuning"],
+                                                       MODES[head]["sweep"] in (1, 2, 4))),
         "roofline": dict(roofline, sweep=res["sweep"]),
         "peaks": peaks,
         "clocks": res["clocks"],

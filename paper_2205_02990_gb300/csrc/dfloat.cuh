@@ -27,8 +27,24 @@ __device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {   // needs
   return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
 
-// The double-float nearest to an FP64 value (to ~2^-48 relative; FP32 exponent range).
+// An FP64 value as a double-float (to ~2^-48 relative; FP32 exponent range), by integer
+// operations on its bits: hi is x truncated to 24 significant bits, lo the remaining 29 bits
+// rounded to FP32 (|lo| < ulp(hi)). On GB300 every FP64 instruction, a conversion included,
+// runs at 1/64 of the FP32 rate, so the common case stays off the FP64 pipe; zeros and values
+// whose hi or lo would leave FP32's normal range take the FP64 conversions.
 __device__ __forceinline__ dfloat df_from(double x) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((u >> 52) & 0x7ff);            // biased exponent
+  if (e >= 1075 - 126 && e <= 1023 + 127) {          // 2^(e - 1075) and hi both FP32-normal
+    const unsigned sign = static_cast<unsigned>(u >> 32) & 0x80000000u;
+    const unsigned mhi = static_cast<unsigned>((u >> 29) & 0x7fffffu);
+    const float hi = __int_as_float(static_cast<int>(sign | (static_cast<unsigned>(e - 1023 + 127) << 23) | mhi));
+    const unsigned rem = static_cast<unsigned>(u & 0x1fffffffu);
+    // rem 2^(e - 1075): exact scaling of the rounded integer by a power of two
+    const float scale = __int_as_float(static_cast<int>(static_cast<unsigned>(e - 1075 + 127) << 23));
+    const float lo = __fmul_rn(__uint2float_rn(rem), scale);
+    return {hi, sign ? -lo : lo};
+  }
   const float h = __double2float_rn(x);
   return {h, __double2float_rn(x - static_cast<double>(h))};
 }

@@ -11,7 +11,7 @@
 //
 // A in page-locked host memory is streamed through the device in row blocks on a second
 // stream, each block's copy overlapping the products of the previous one: block b gives the
-// rows b of Y and one reduction slice of Z = sum_b A_b^* Psi_b; Z's slices are summed in block
+// rows b of Y and reduction slices of Z = sum_b A_b^* Psi_b; Z's slices are summed in block
 // order at the end.
 #include <algorithm>
 #include <cmath>
@@ -294,25 +294,38 @@ cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, con
 cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, const double* Om,
                                    const double* Ps, int s, double* Y, double* Z,
                                    cudaStream_t st) {
-  // row blocks of ~N/8 rows (a multiple of the 64-row tile), at most 2 GiB of staging each
-  int64_t nb = ((N + 7) / 8 + BM - 1) / BM * BM;
+  // Row blocks (multiples of the 64-row tile) growing from ~N/64 rows by half each time up to
+  // ~N/8 rows (at most 2 GiB of staging each): the first copy, which nothing hides, stays short,
+  // and while the blocks grow each block's products still outlast the next block's copy
+  // whenever the host link carries more than ~2/3 of what the products consume.
   const int64_t cap = std::max<int64_t>(BM, (int64_t(1) << 28) / std::max<int64_t>(1, N) / BM * BM);
-  nb = std::max<int64_t>(BM, std::min(nb, cap));
-  nb = std::min(nb, N);
-  const int64_t nblocks = (N + nb - 1) / nb;
-  int zs = 0;                                          // Z slices per block
-  int64_t zk = 0;
-  plan_slices(N, nb, s, &zs, &zk);
+  const int64_t nb_max = std::min(N, std::max<int64_t>(BM, std::min(((N + 7) / 8 + BM - 1) / BM * BM, cap)));
+  std::vector<int64_t> rows_of;
+  std::vector<int> zs_of;
+  int64_t total_slices = 0;
+  for (int64_t r0 = 0, nb = std::min(nb_max, ((N + 63) / 64 + BM - 1) / BM * BM); r0 < N;) {
+    const int64_t rows = std::min(nb, N - r0);
+    int zs = 0;                                        // Z slices of this block
+    int64_t zk = 0;
+    plan_slices(N, rows, s, &zs, &zk);
+    rows_of.push_back(rows);
+    zs_of.push_back(zs);
+    total_slices += zs;
+    r0 += rows;
+    nb = std::min(nb_max, (nb + nb / 2 + BM - 1) / BM * BM);
+  }
   const int64_t count = N * s;
   HostStream* h = nullptr;
-  cudaError_t e = host_stream(static_cast<size_t>(nb) * N,
-                              static_cast<size_t>(nblocks) * zs * count, &h);
+  cudaError_t e = host_stream(static_cast<size_t>(nb_max) * N,
+                              static_cast<size_t>(total_slices) * count, &h);
   if (e != cudaSuccess) return e;
   e = cudaEventRecord(h->start, st);                   // the stages are free once st is here
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy, h->start, 0);
-  for (int64_t b = 0; b < nblocks && e == cudaSuccess; ++b) {
+  int64_t r0 = 0, slice0 = 0;
+  for (size_t b = 0; b < rows_of.size() && e == cudaSuccess; ++b) {
     const int slot = static_cast<int>(b & 1);
-    const int64_t r0 = b * nb, rows = std::min(nb, N - r0);
+    const int64_t rows = rows_of[b];
+    const int zs = zs_of[b];
     if (b >= 2) e = cudaStreamWaitEvent(h->copy, h->consumed[slot], 0);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(h->stage[slot], N * sizeof(double), A + r0 * lda, lda * sizeof(double),
@@ -321,16 +334,17 @@ cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, cons
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->copied[slot], 0);
     if (e == cudaSuccess) e = product(false, h->stage[slot], N, rows, N, Om, s, Y + r0 * s, st);
     if (e == cudaSuccess) {
-      // zs slices for every block (a short last block leaves some empty: they write zeros)
       const int64_t zkb = ((rows + zs - 1) / zs + BK - 1) / BK * BK;
-      double* zb = h->zpart + static_cast<size_t>(b) * zs * count;
+      double* zb = h->zpart + static_cast<size_t>(slice0) * count;
       e = launch_slices(true, h->stage[slot], N, N, rows, Ps + r0 * s, s, zb, zs, zkb, count, st);
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->consumed[slot], st);
+    r0 += rows;
+    slice0 += zs;
   }
   if (e != cudaSuccess) return e;
   const unsigned rg = static_cast<unsigned>(std::min<int64_t>((count + 255) / 256, 8 * sm_count()));
-  sum_slices<<<rg, 256, 0, st>>>(h->zpart, static_cast<int>(nblocks) * zs, count, Z);
+  sum_slices<<<rg, 256, 0, st>>>(h->zpart, static_cast<int>(total_slices), count, Z);
   return cudaGetLastError();
 }
 

@@ -22,10 +22,10 @@
 //
 // Accumulation. The diagonal d of a window is one accumulator in tensor memory (four of them,
 // several): the MMA thread fills one while eight drain warps scale another by its power of
-// two (exact) and add it to a double-float running sum kept in registers (hi + lo: TwoSum in
-// FP32, then a Fast2Sum renormalisation that keeps |lo| <= ulp(hi) / 2, so that every addition
-// errs by at most ~2^-48 of the running sum). A CTA's reduction range is at most 32 windows (2048 indices); the ranges are summed
-// in FP64 by the reduce kernel. Within a range, scales are taken relative to the largest block
+// two (exact) and add it to a double-float running sum kept in registers (hi + lo: the leading
+// diagonals by TwoSum in FP32, hi exact and its rounding error collected in lo; the trailing
+// ones, far below the sum, by one FMA into lo). A CTA's reduction range is at most 32 windows
+// (2048 indices); the ranges are summed in FP64 by the reduce kernel. Within a range, scales are taken relative to the largest block
 // exponents of the output row's entries of A and of the test matrix over that range; the
 // reduce kernel scales each range's sum back in FP64. Every output row keeps the full FP64
 // exponent range; only blocks more than ~2^100 below the largest block of their row and range
@@ -294,8 +294,12 @@ struct OzArgs {
 };
 
 constexpr int kAccBufs = 4;          // accumulators in tensor memory, 128 columns each
-constexpr int kExactDiags = 4;       // diagonals added by TwoSum; the later ones weigh < 2^-30 of
-                                     // d = 0 and go into lo with one FMA (error < 2^-48 of hi)
+// Diagonals added to the running sum by TwoSum (hi exact, its rounding error into lo); the later
+// ones weigh < 2^-8 kExactDiags of diagonal 0 and go into lo with one FMA. FP64-class products
+// (S >= 6) take 4 (later terms < 2^-32 of the sum, each rounded to 2^-56 of it); the 5-digit
+// products, whose own truncation is ~2^-38, take 3 (later terms < 2^-24, rounded to 2^-48).
+template <int S>
+__host__ __device__ constexpr int exact_diags() { return S >= 6 ? 4 : 3; }
 constexpr int kEmptyRange = -(1 << 20);
 
 __device__ __forceinline__ float pow2f(int e) {
@@ -311,6 +315,17 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
   const float h2 = __fadd_rn(s, t);
   lo = __fsub_rn(t, __fsub_rn(h2, s));
   hi = h2;
+}
+
+// hi += v exactly by TwoSum, the rounding error of hi added to lo (no renormalisation: each
+// error is at most ulp(hi) / 2, so over the <= 32 windows of a split |lo| stays below ~2^6 ulp(hi)
+// and its own roundings below 2^-40 of hi).
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+  hi = s;
+  lo = __fadd_rn(lo, err);
 }
 
 template <bool ACC>
@@ -524,10 +539,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           if (c >= nchunks) continue;
           uint32_t x[16];
           tmem_ld16(tmem + lane_base + static_cast<uint32_t>(b * 128 + 16 * c), x);
-          if (d < kExactDiags) {
+          if (d < exact_diags<S>()) {
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              df_add(hi[cc][j], lo[cc][j], __fmul_rn(__uint_as_float(x[j]), scale));
+              two_sum_acc(hi[cc][j], lo[cc][j], __fmul_rn(__uint_as_float(x[j]), scale));
           } else {                                        // below 2^-30 of the running sum
 #pragma unroll
             for (int j = 0; j < 16; ++j) lo[cc][j] = __fmaf_rn(__uint_as_float(x[j]), scale, lo[cc][j]);

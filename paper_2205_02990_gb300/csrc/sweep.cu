@@ -650,11 +650,11 @@ __device__ __forceinline__ double to_f64(dfloat v) { return df_to(v); }
 // of TM rows and 32 TN columns, lane l the columns l, l + 32, ...: a(i, k) is the same for the
 // whole warp (one broadcast) and b(k, j) is read by consecutive lanes (no bank conflicts), so
 // each k costs TM + TN shared loads per warp for 32 TM TN multiply-adds.
-template <class Real, int TM, int TN, class FA, class FB, class FI, class FO>
+template <class Real, int TM, int TN, int NT = THREADS, class FA, class FB, class FI, class FO>
 __device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI init, FO out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tn = (N + 32 * TN - 1) / (32 * TN), tm = (M + TM - 1) / TM;
-  for (int t = warp; t < tm * tn; t += THREADS / 32) {
+  for (int t = warp; t < tm * tn; t += NT / 32) {
     const int i0 = (t / tn) * TM, j0 = (t % tn) * 32 * TN + lane;
     Real acc[TM][TN];
 #pragma unroll
@@ -689,8 +689,10 @@ __device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI in
 // stores those as FP64; Real = dfloat stores them, and U and V, as double-float pairs (two
 // floats in each 8-byte slot: U^* D and (D V)^* in XY, XZ; U, V in the spent WY, WZ), so that
 // node_merge_r<dfloat> reads them without converting again.
+constexpr int kDchainThreads = 512;   // 16 warps: one CTA per SM (its tile fills the shared memory)
+
 template <class Real>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(kDchainThreads, 1)
     node_dchain(const NodeTask* __restrict__ tasks) {
   extern __shared__ __align__(16) unsigned char dch_bytes[];
   Real* fsm = reinterpret_cast<Real*>(dch_bytes);
@@ -704,38 +706,38 @@ __global__ void __launch_bounds__(THREADS, 1)
   Real* Vs = Us + static_cast<size_t>(n) * r;          // n x r
   Real* T2 = Vs + static_cast<size_t>(n) * r;          // n x ldT: WZ, then (I - VV^*) WZ, then D
   Real* WYs = T2 + static_cast<size_t>(n) * ldT;       // n x n
-  for (int e = threadIdx.x; e < n * r; e += THREADS) {
+  for (int e = threadIdx.x; e < n * r; e += kDchainThreads) {
     Us[e] = from_f64<Real>(tk.U[e]);
     Vs[e] = from_f64<Real>(tk.V[e]);
   }
-  for (int e = threadIdx.x; e < n * n; e += THREADS) {
+  for (int e = threadIdx.x; e < n * n; e += kDchainThreads) {
     WYs[e] = from_f64<Real>(tk.WY[e]);
     T2[(e / n) * ldT + e % n] = from_f64<Real>(tk.WZ[e]);
   }
   __syncthreads();
   // G1 = V^* WZ (r x n)
-  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int i) { return Vs[i * r + c]; },
+  tile_gemm<Real, 4, 1, kDchainThreads>(r, n, n, [&](int c, int i) { return Vs[i * r + c]; },
                         [&](int i, int j) { return T2[i * ldT + j]; }, [](int, int) { return Real{}; },
                         [&](int c, int j, Real v) { G1[c * ldX + j] = v; });
   __syncthreads();
   // T2 = WZ - V G1 (n x n), in place: each entry reads only its own WZ value
-  tile_gemm<Real, 8, 1>(n, n, r, [&](int i, int c) { return nneg(Vs[i * r + c]); },
+  tile_gemm<Real, 8, 1, kDchainThreads>(n, n, r, [&](int i, int c) { return nneg(Vs[i * r + c]); },
                         [&](int c, int j) { return G1[c * ldX + j]; },
                         [&](int i, int j) { return T2[i * ldT + j]; },
                         [&](int i, int j, Real v) { T2[i * ldT + j] = v; });
   __syncthreads();
   // G1 = U^* T2^* (= U^* D), then Hs = G1 - U^* WY
-  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int i) { return Us[i * r + c]; },
+  tile_gemm<Real, 4, 1, kDchainThreads>(r, n, n, [&](int c, int i) { return Us[i * r + c]; },
                         [&](int i, int j) { return T2[j * ldT + i]; }, [](int, int) { return Real{}; },
                         [&](int c, int j, Real v) { G1[c * ldX + j] = v; });
   __syncthreads();
-  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int i) { return nneg(Us[i * r + c]); },
+  tile_gemm<Real, 4, 1, kDchainThreads>(r, n, n, [&](int c, int i) { return nneg(Us[i * r + c]); },
                         [&](int i, int j) { return WYs[i * n + j]; },
                         [&](int c, int j) { return G1[c * ldX + j]; },
                         [&](int c, int j, Real v) { Hs[c * n + j] = v; });
   __syncthreads();
   // D = WY + U Hs (n x n), stored as FP64 and kept in T2
-  tile_gemm<Real, 8, 1>(n, n, r, [&](int i, int c) { return Us[i * r + c]; },
+  tile_gemm<Real, 8, 1, kDchainThreads>(n, n, r, [&](int i, int c) { return Us[i * r + c]; },
                         [&](int c, int j) { return Hs[c * n + j]; },
                         [&](int i, int j) { return WYs[i * n + j]; },
                         [&](int i, int j, Real v) {
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         });
   __syncthreads();
   // Hs = (D V)^* (r x n)
-  tile_gemm<Real, 4, 1>(r, n, n, [&](int c, int j) { return Vs[j * r + c]; },
+  tile_gemm<Real, 4, 1, kDchainThreads>(r, n, n, [&](int c, int j) { return Vs[j * r + c]; },
                         [&](int j, int i) { return T2[i * ldT + j]; }, [](int, int) { return Real{}; },
                         [&](int c, int i, Real v) { Hs[c * n + i] = v; });
   __syncthreads();
@@ -753,7 +755,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     Real* XZd = reinterpret_cast<Real*>(tk.XZ);
     Real* Ud = reinterpret_cast<Real*>(tk.WY);
     Real* Vd = reinterpret_cast<Real*>(tk.WZ);
-    for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    for (int e = threadIdx.x; e < r * n; e += kDchainThreads) {
       const int c = e / n, i = e % n;
       XYd[e] = G1[c * ldX + i];
       XZd[e] = Hs[e];
@@ -761,7 +763,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       Vd[e] = Vs[e];
     }
   } else {
-    for (int e = threadIdx.x; e < r * n; e += THREADS) {
+    for (int e = threadIdx.x; e < r * n; e += kDchainThreads) {
       const int c = e / n, i = e % n;
       tk.XY[e] = to_f64(G1[c * ldX + i]);
       tk.XZ[e] = to_f64(Hs[e]);
@@ -936,6 +938,9 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
   if (side_bytes > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
   const int splits = std::max(1, std::min(R, std::max(1, max_n)));
+  // four or three CTAs per SM where that many tiles (plus the 1 KB the runtime reserves per
+  // CTA) fit; the register budget follows (64, 80 or 128 per thread, no spills)
+  const int fit = static_cast<int>((228 * 1024) / (side_bytes + 1024));
   const dim3 grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
   auto side = [&](auto kernel) {
     e = allow_smem(kernel);
@@ -944,9 +949,6 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
       e = cudaGetLastError();
     }
   };
-  // four or three CTAs per SM where that many tiles (plus the 1 KB the runtime reserves per
-  // CTA) fit; the register budget follows (64, 80 or 128 per thread, no spills)
-  const int fit = static_cast<int>((228 * 1024) / (side_bytes + 1024));
   if (max_s <= 8 * G) {
     if (fit >= 4) side(node_side<8, 4>);
     else if (fit == 3) side(node_side<8, 3>);
@@ -1015,7 +1017,7 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
     auto finish_pair = [&](auto dchain, auto merge) {
       e = allow_smem(dchain);
       if (e != cudaSuccess) return;
-      dchain<<<ntasks, THREADS, dblk_bytes, st>>>(d_tasks);
+      dchain<<<ntasks, kDchainThreads, dblk_bytes, st>>>(d_tasks);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = mark(3);
       if (e != cudaSuccess) return;

@@ -321,3 +321,22 @@ def test_profile_sweep_times_every_phase_and_keeps_factors(hb):
         for u, v in zip(a, b):
             assert (u is None and v is None) or torch.equal(u, v)
     h.free()
+
+
+def test_full_size_tree_every_factor_matches_oracle(hb):
+    # The headline tree (N = 32768, r = 40, s = 120, leaf 64: 1023 nodes over 10 levels, the
+    # same launches and tuned side shapes as the benchmark) on well-conditioned inputs, where the
+    # factors are determined to rounding (the log kernel's are not: reading A22), so every U, V,
+    # D of every node is held to the FP64 bar against the oracle.
+    N, r, s, leaf = 32768, 40, 120, 64
+    x = [gaussian((N, s), 5100 + i) for i in range(4)]
+    F, blk = ocompress(*x, r, leaf, keep_blocks=True)
+    tens = [dev(v) for v in x]
+    h = hb.hbs_plan([hb.Problem(N, r, s, leaf, *tens)])
+    hb.hbs_execute(h)
+    hb.hbs_autotune(h)                                 # the benchmark's tuned shapes
+    hb.hbs_execute(h)
+    hb.hbs_sync_status(h)
+    worst, where = factor_errors(hb, h, F, blk, range(1, 2 ** (F.L + 1)))
+    assert worst <= 1e-10, (worst, where)
+    h.free()
