@@ -636,7 +636,9 @@ __global__ void __launch_bounds__(THREADS)
 // finish) or dfloat (double-float, the compensated finish). Loads convert once from FP64, stores
 // convert back.
 __device__ __forceinline__ float nfma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ dfloat nfma(dfloat a, dfloat b, dfloat c) { return df_fma(a, b, c); }
+__device__ __forceinline__ dfloat nfma(dfloat a, dfloat b, dfloat c) { return df_fma_acc(a, b, c); }
+__device__ __forceinline__ float nfinish(float a) { return a; }
+__device__ __forceinline__ dfloat nfinish(dfloat a) { return df_norm(a); }
 __device__ __forceinline__ float nneg(float a) { return -a; }
 __device__ __forceinline__ dfloat nneg(dfloat a) { return df_neg(a); }
 template <class Real> __device__ __forceinline__ Real from_f64(double x);
@@ -677,7 +679,7 @@ __device__ __forceinline__ void tile_gemm(int M, int N, int K, FA a, FB b, FI in
     for (int ii = 0; ii < TM; ++ii)
 #pragma unroll
       for (int jj = 0; jj < TN; ++jj)
-        if (i0 + ii < M && j0 + 32 * jj < N) out(i0 + ii, j0 + 32 * jj, acc[ii][jj]);
+        if (i0 + ii < M && j0 + 32 * jj < N) out(i0 + ii, j0 + 32 * jj, nfinish(acc[ii][jj]));
   }
 }
 
@@ -825,11 +827,15 @@ __global__ void __launch_bounds__(THREADS)
   tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return Bts[i * r + c]; },
                         [&](int i, int k) { return Ts[i * kw + k]; }, [](int, int) { return Real{}; },
                         [&](int c, int k, Real v) { outT[c * s + k0 + k] = to_f64(v); });
-  // U^* S - H T as one product over 2n: [Bs^*, -H] [S; T]
-  tile_gemm<Real, 2, 1>(r, kw, 2 * n,
-                        [&](int c, int i) { return i < n ? Bss[i * r + c] : nneg(Hsm[c * n + i - n]); },
-                        [&](int i, int k) { return i < n ? Ss[i * kw + k] : Ts[(i - n) * kw + k]; },
-                        [](int, int) { return Real{}; },
+  // U^* S - H T as two products: Pm = U^* S, then Pm - H T
+  Real* Pm = Hsm + static_cast<size_t>(r) * n;         // r x kw
+  tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return Bss[i * r + c]; },
+                        [&](int i, int k) { return Ss[i * kw + k]; }, [](int, int) { return Real{}; },
+                        [&](int c, int k, Real v) { Pm[c * kw + k] = v; });
+  __syncthreads();
+  tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return nneg(Hsm[c * n + i]); },
+                        [&](int i, int k) { return Ts[i * kw + k]; },
+                        [&](int c, int k) { return Pm[c * kw + k]; },
                         [&](int c, int k, Real v) { outS[c * s + k0 + k] = to_f64(v); });
 }
 
@@ -866,7 +872,8 @@ size_t dchain_smem_reals(int n, int r) {
          static_cast<size_t>(n) * n;
 }
 size_t merge_r_smem_reals(int n, int r, int chunk) {
-  return 2 * static_cast<size_t>(n) * chunk + 3 * static_cast<size_t>(n) * r;
+  return 2 * static_cast<size_t>(n) * chunk + 3 * static_cast<size_t>(n) * r +
+         static_cast<size_t>(r) * chunk;
 }
 
 // The largest shared-memory tile the sweep kernels need for a node of n rows.
