@@ -39,8 +39,19 @@ SM_COUNT_GB300 = 152
 FP64_DFMA_PER_CLK_PER_SM = 2          # GB300: FP64 at 1/64 of the FP32 rate (1.25 TF nominal)
 GEMM_READ_8192 = 549.46e6             # dram bytes read by one sample_gemm_f64 launch, N = 8192
 GEMM_WRITE_8192 = 42.30e6             # dram bytes written (split-K partials) by that launch
-BF16_TFLOPS_SUSTAINED = 1666.9        # measured dense bf16 peak on this machine's GB300 (sustained)
-HBM_GBS = 6782.1                      # measured copy bandwidth on this machine's GB300
+def measured_peaks():
+    """Dense bf16 (sustained) and HBM copy peaks measured on the GB300s
+    (MEASURED_PEAKS.json beside this file, written by the pool's driver), else the fallback of one
+    earlier GB300 measurement (1.7 PFLOP/s sustained, 6.8 TB/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1700.0, 6800.0, "fallback"
+
+
+BF16_TFLOPS_SUSTAINED, HBM_GBS, PEAKS_SOURCE = measured_peaks()
 FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # derived FP64 peak: SMs x DFMA/clk x 2 flop x clock
 DF32_SLOTS = 15                       # FP32 instructions of one double-float multiply-add
 
@@ -351,7 +362,7 @@ def peaks_now(hb):
     fp32 = SM_COUNT_GB300 * 128 * 2 * 2070e6 / 1e12
     return {"fp64_derived": FP64_TFLOPS, "fp32_derived": fp32,
             "df32_derived": fp32 / DF32_SLOTS, "fp64_probe": fp64_probe, "fp32_probe": fp32_probe,
-            "df32_from_probe": fp32_probe / DF32_SLOTS}
+            "df32_from_probe": fp32_probe / DF32_SLOTS, "fp64_dmma_probe": hb.hbs_probe_dmma()}
 
 
 def sweep_roofline(phase_ms, N, r, s, leaf, finish, peaks):
@@ -892,7 +903,7 @@ def main():
                               f"{pairs} exact FP16 digit-pair products)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+                    "peak_source": f"bf16_tflops_sustained (of {PEAKS_SOURCE})"}
     elif MODES[head]["sample"] == 0:
         peak = SM_COUNT_GB300 * FP64_DFMA_PER_CLK_PER_SM * 2 * 2070e6 / 1e12
         achieved = flops_product / res["per_launch"] / 1e12
@@ -910,7 +921,7 @@ def main():
         roofline = {"kernel": "sliced_gemm_tc (bf16x6: 6 slice products per FP32 product)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)"}
+                    "peak_source": f"bf16_tflops_sustained (of {PEAKS_SOURCE})"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3,

@@ -303,6 +303,11 @@ int hbs_copy_factors(const hbs_handle* h, void* dst, void* cuda_stream);
  */
 int hbs_probe_peaks(double* fp64_tflops, double* fp32_tflops, void* cuda_stream);
 
+/* The same for the FP64 tensor instruction (mma.sync m8n8k4 with FP64 operands, 512 flops per
+ * warp instruction), in TFLOP/s; this library does not use it (it shares the FP64 units' rate).
+ * Synchronizes cuda_stream; allocates 16 bytes. Errors: HBS_ERR_ARG, HBS_ERR_NOMEM, HBS_ERR_CUDA. */
+int hbs_probe_dmma(double* tflops, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------------------
  * Apply without allocating (no counterpart in the paper; a service of this library).
  *

@@ -776,8 +776,13 @@ __global__ void __launch_bounds__(kDchainThreads, 1)
 // Merges (Eq. omega_tau_and_y_tau): grid (node, chunk of kw columns, pass) as node_merge, from U,
 // V and the products U^* D, (D V)^* that node_dchain left behind; the chunk, the bases and the
 // product are staged in shared memory.
+// Threads of the merges: 256 in FP32 (three CTAs per SM fit), 512 in double-float, whose 8-byte
+// tiles at n = 80 leave one CTA per SM.
 template <class Real>
-__global__ void __launch_bounds__(THREADS)
+__host__ __device__ constexpr int merge_threads() { return sizeof(Real) == sizeof(double) ? 512 : THREADS; }
+
+template <class Real>
+__global__ void __launch_bounds__(merge_threads<Real>())
     node_merge_r(const NodeTask* __restrict__ tasks, int chunk) {
   extern __shared__ __align__(16) unsigned char mr_bytes[];
   Real* msf = reinterpret_cast<Real*>(mr_bytes);
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(THREADS)
   Real* Bts = Ss + static_cast<size_t>(n) * kw;        // n x r: reduces the test block
   Real* Bss = Bts + static_cast<size_t>(n) * r;        // n x r: reduces the sample block
   Real* Hsm = Bss + static_cast<size_t>(n) * r;        // r x n: (D V)^* or U^* D
-  for (int e = threadIdx.x; e < n * kw; e += THREADS) {
+  for (int e = threadIdx.x; e < n * kw; e += merge_threads<Real>()) {
     const int i = e / kw, k = e % kw;
     Ts[e] = from_f64<Real>(T[static_cast<size_t>(i) * s + k0 + k]);
     Ss[e] = from_f64<Real>(S[static_cast<size_t>(i) * s + k0 + k]);
@@ -808,7 +813,7 @@ __global__ void __launch_bounds__(THREADS)
     const Real* H = reinterpret_cast<const Real*>(pass ? tk.XZ : tk.XY);
     const Real* Bt = pass ? Ud : Vd;
     const Real* Bs = pass ? Vd : Ud;
-    for (int e = threadIdx.x; e < n * r; e += THREADS) {
+    for (int e = threadIdx.x; e < n * r; e += merge_threads<Real>()) {
       Bts[e] = Bt[e];
       Bss[e] = Bs[e];
       Hsm[e] = H[e];
@@ -817,26 +822,30 @@ __global__ void __launch_bounds__(THREADS)
     const double* Bt = pass ? tk.U : tk.V;
     const double* Bs = pass ? tk.V : tk.U;
     const double* H = pass ? tk.XZ : tk.XY;
-    for (int e = threadIdx.x; e < n * r; e += THREADS) {
+    for (int e = threadIdx.x; e < n * r; e += merge_threads<Real>()) {
       Bts[e] = from_f64<Real>(Bt[e]);
       Bss[e] = from_f64<Real>(Bs[e]);
       Hsm[e] = from_f64<Real>(H[e]);
     }
   }
   __syncthreads();
-  tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return Bts[i * r + c]; },
+  tile_gemm<Real, 2, 1, merge_threads<Real>()>(r, kw, n, [&](int c, int i) { return Bts[i * r + c]; },
                         [&](int i, int k) { return Ts[i * kw + k]; }, [](int, int) { return Real{}; },
                         [&](int c, int k, Real v) { outT[c * s + k0 + k] = to_f64(v); });
   // U^* S - H T as two products: Pm = U^* S, then Pm - H T
   Real* Pm = Hsm + static_cast<size_t>(r) * n;         // r x kw
-  tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return Bss[i * r + c]; },
+  tile_gemm<Real, 2, 1, merge_threads<Real>()>(r, kw, n, [&](int c, int i) { return Bss[i * r + c]; },
                         [&](int i, int k) { return Ss[i * kw + k]; }, [](int, int) { return Real{}; },
                         [&](int c, int k, Real v) { Pm[c * kw + k] = v; });
   __syncthreads();
-  tile_gemm<Real, 2, 1>(r, kw, n, [&](int c, int i) { return nneg(Hsm[c * n + i]); },
+  tile_gemm<Real, 2, 1, merge_threads<Real>()>(r, kw, n, [&](int c, int i) { return nneg(Hsm[c * n + i]); },
                         [&](int i, int k) { return Ts[i * kw + k]; },
                         [&](int c, int k) { return Pm[c * kw + k]; },
                         [&](int c, int k, Real v) { outS[c * s + k0 + k] = to_f64(v); });
+}
+
+int merge_threads_of(int finish) {
+  return finish == kFinishF32 ? merge_threads<float>() : merge_threads<dfloat>();
 }
 
 template <class Kernel>
@@ -1030,7 +1039,7 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
       if (e != cudaSuccess) return;
       e = allow_smem(merge);
       if (e != cudaSuccess) return;
-      merge<<<merge_grid, THREADS, merge_bytes, st>>>(d_tasks, chunk);
+      merge<<<merge_grid, merge_threads_of(finish), merge_bytes, st>>>(d_tasks, chunk);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = mark(4);
     };

@@ -37,7 +37,7 @@ EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan"
             "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
             "hbs_apply_static", "hbs_sample_sync", "hbs_apply_batch", "hbs_load_factors",
             "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph",
-            "hbs_test_inject_status", "hbs_probe_peaks", "hbs_profile_sweep"]
+            "hbs_test_inject_status", "hbs_probe_peaks", "hbs_profile_sweep", "hbs_probe_dmma"]
 
 
 class HBSError(RuntimeError):
@@ -96,6 +96,7 @@ def load():
         "hbs_sync_status": (c.c_int, [c.c_void_p, c.c_void_p]),
         "hbs_test_inject_status": (c.c_int, [c.c_void_p, c.c_int32]),
         "hbs_probe_peaks": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_double), c.c_void_p]),
+        "hbs_probe_dmma": (c.c_int, [c.POINTER(c.c_double), c.c_void_p]),
         "hbs_profile_sweep": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int32,
                                         c.POINTER(c.c_int32)]),
         "hbs_free": (None, [c.c_void_p]),
@@ -387,6 +388,13 @@ def hbs_probe_peaks():
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(load().hbs_probe_peaks(ctypes.byref(a), ctypes.byref(b), _stream()))
     return a.value, b.value
+
+
+def hbs_probe_dmma():
+    """FP64 tensor-instruction (DMMA) throughput of the current GPU in TFLOP/s (measured now)."""
+    a = ctypes.c_double()
+    _check(load().hbs_probe_dmma(ctypes.byref(a), _stream()))
+    return a.value
 
 
 def hbs_free(handle):
