@@ -165,14 +165,41 @@ __device__ __forceinline__ uint32_t digit_pair_f16(uint32_t l0, uint32_t h0, uin
   return *reinterpret_cast<const uint32_t*>(&d);
 }
 
+// V for one entry of a block whose exponent E lies above 8S - 1020: there every subnormal
+// entry (< 2^-1022) scales to below 1/2 and rounds to 0, so one select replaces the general
+// form's test. Normal entries take the integer path of offset_value (t >= 56 - 8S >= 0 since the
+// entry is below 2^(E-1)); an Inf or NaN, already flagged by the block exponent, gives a value
+// that is not used.
+template <int S>
+__device__ __forceinline__ void offset_value_normal(double x, int E, uint32_t& vl, uint32_t& vh) {
+  const uint32_t lx = static_cast<uint32_t>(__double2loint(x));
+  const uint32_t hx = static_cast<uint32_t>(__double2hiint(x));
+  const int ex = static_cast<int>((hx >> 20) & 0x7ffu);
+  const uint32_t mh = (hx & 0xfffffu) | 0x100000u;
+  const uint64_t u = ((static_cast<uint64_t>(mh) << 32) | lx) << 3;
+  const int t = min(63, E + 1077 - 8 * S - ex);
+  const uint64_t X = ex == 0 ? 0ull : ((u >> t) + 1) >> 1;
+  const uint64_t V = (hx >> 31) ? digit_offset<S>() - X : digit_offset<S>() + X;
+  vl = static_cast<uint32_t>(V);
+  vh = static_cast<uint32_t>(V >> 32);
+}
+
+template <int S>
+__device__ __forceinline__ bool block_is_normal(int E) { return E > 8 * S - 1020; }
+
 // FP16 digits of two neighbouring entries into S planes (plane_stride apart), one 32-bit store
-// per plane.
+// per plane. E is the same for the whole warp, so the choice of path is warp-uniform.
 template <int S>
 __device__ __forceinline__ void store_digit_pair(double x0, double x1, int E, uint16_t* dst,
                                                  size_t plane_stride) {
   uint32_t l0, h0, l1, h1;
-  offset_value<S>(x0, E, l0, h0);
-  offset_value<S>(x1, E, l1, h1);
+  if (block_is_normal<S>(E)) {
+    offset_value_normal<S>(x0, E, l0, h0);
+    offset_value_normal<S>(x1, E, l1, h1);
+  } else {
+    offset_value<S>(x0, E, l0, h0);
+    offset_value<S>(x1, E, l1, h1);
+  }
 #pragma unroll
   for (int i = 0; i < S; ++i)
     *reinterpret_cast<uint32_t*>(dst + i * plane_stride) = digit_pair_f16<S>(l0, h0, l1, h1, i);
@@ -271,7 +298,8 @@ __global__ void __launch_bounds__(256)
     const int64_t k = k0 + kk;
     const double x = (c < s && k < N) ? X[k * s + c] : 0.0;
     uint32_t vl, vh;
-    offset_value<S>(x, E, vl, vh);
+    if (block_is_normal<S>(E)) offset_value_normal<S>(x, E, vl, vh);
+    else offset_value<S>(x, E, vl, vh);
 #pragma unroll
     for (int i = 0; i < S; ++i)
       out[i * plane + static_cast<size_t>(c) * ldd + k] =
