@@ -121,8 +121,17 @@ def sweep_launches(N, r, s, leaf, tuning, reduced):
     return len(tuning) * ((1 + 3) if reduced else (1 + 4))
 
 
+def df32_fits(n, r):
+    """Whether the double-float D and merge tiles of nodes of n rows fit 227 KB of shared memory
+    (the library runs the FP64 finish on heights where they do not)."""
+    dchain = r * (n + 1) + r * n + 2 * n * r + n * (n + 1) + n * n
+    merge = 2 * n * 32 + 3 * n * r + r * 32
+    return 8 * max(dchain, merge) <= 227 * 1024
+
+
 def sweep_phase_flops(N, r, s, leaf, reduced):
-    """Per height (finest first): flops of the side, bases, D and merge phases."""
+    """Per height (finest first): flops of the side, bases, D and merge phases. ``reduced`` is
+    False (FP64 finish), "fp32" or "df32"."""
     L = tree_nodes(N, leaf)
     out = []
     for level in range(L, -1, -1):
@@ -140,11 +149,12 @@ def sweep_phase_flops(N, r, s, leaf, reduced):
             out.append([side_flops(n, s), 0.0, 0.0, 0.0])
             continue
         ph = [0.0, 0.0, 0.0, 0.0]
+        red = bool(reduced) and (reduced != "df32" or df32_fits(max(n for n, _ in groups), r))
         for n, c in groups:
             ph[0] += c * 2 * side_flops(n, s)
             ph[1] += c * 2 * bases_flops(n, r)
-            ph[2] += c * d_flops(n, r, reduced)
-            ph[3] += c * merge_flops(n, r, s, reduced)
+            ph[2] += c * d_flops(n, r, red)
+            ph[3] += c * merge_flops(n, r, s, red)
         out.append(ph)
     return out
 
@@ -265,10 +275,11 @@ def dist_env():
 # ------------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the workload (cpu_baseline and --impl reference)
 
-def oracle_sample_time(N, r, s, leaf, rows=4096, sweep_N=8192, workload="logkernel"):
+def oracle_sample_time(N, r, s, leaf, rows=4096, sweep_N=8192, workload="logkernel", measured=None):
     """Seconds the FP64 oracle would take for the full workload, from a bounded sample:
     Philox rows and sampling products for ``rows`` of the N rows, and the sweep of a
-    ``sweep_N``-point problem of the same r, s, leaf, each scaled by its share of the work."""
+    ``sweep_N``-point problem of the same r, s, leaf, each scaled by its share of the work.
+    With ``measured`` (a list), the sample's own seconds are appended to it."""
     import numpy as np
     from hbs_inputs import double_layer_rows, gaussian, log_kernel_rows
     from oracle import philox
@@ -280,15 +291,19 @@ def oracle_sample_time(N, r, s, leaf, rows=4096, sweep_N=8192, workload="logkern
     t0 = time.perf_counter()
     Om_rows = philox.gaussian_matrix(N, s, 0, SEED, rows=idx)
     Ps_rows = philox.gaussian_matrix(N, s, 1, SEED, rows=idx)
-    t_rng = (time.perf_counter() - t0) * N / rows
+    m_rng = time.perf_counter() - t0
     Om = np.tile(Om_rows, (N // rows + 1, 1))[:N]           # full-height Omega stand-in
     t0 = time.perf_counter()
     sample_dense(A_rows, Om, Ps_rows)                        # rows x N block of both products
-    t_smp = (time.perf_counter() - t0) * N / rows
+    m_smp = time.perf_counter() - t0
     x = [gaussian((sweep_N, s), 17 + i) for i in range(4)]
     t0 = time.perf_counter()
     compress(*x, r, leaf)
-    t_sw = (time.perf_counter() - t0) * sweep_flops(N, r, s, leaf) / sweep_flops(sweep_N, r, s, leaf)
+    m_sw = time.perf_counter() - t0
+    if measured is not None:
+        measured.append(m_rng + m_smp + m_sw)
+    t_rng, t_smp = m_rng * N / rows, m_smp * N / rows
+    t_sw = m_sw * sweep_flops(N, r, s, leaf) / sweep_flops(sweep_N, r, s, leaf)
     sample = (f"Philox draws and both sampling products for {rows} of {N} rows, sweep of a "
               f"{sweep_N}-point problem (r={r}, s={s}, leaf {leaf}); scaled to N={N} by rows and "
               f"by sweep flops")
@@ -308,16 +323,21 @@ def run_reference(args, N, r, s, leaf):
         return
     for _ in range(args.warmup):
         oracle_sample_time(N, r, s, leaf)
-    times, sample = [], ""
+    times, measured, sample = [], [], ""
     wall0 = time.perf_counter()
     for _ in range(args.steps):
-        t, sample = oracle_sample_time(N, r, s, leaf)
+        t, sample = oracle_sample_time(N, r, s, leaf, measured=measured)
         times.append(t)
     wall = time.perf_counter() - wall0
     t = statistics.mean(times)
     value = N * s / t
+    # a step is one bounded sample of the workload: its time is what the step took, and its work
+    # is the fraction of a full step that the sample represents (value x time = work done)
+    step_s = statistics.mean(measured)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "work_fraction_per_step": step_s / t, "ms_per_full_step_scaled": t * 1e3,
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": f"log-kernel N={N} r={r} s={s} leaf={leaf} FP64 dense",
@@ -370,8 +390,7 @@ def sweep_roofline(phase_ms, N, r, s, leaf, finish, peaks):
     (sweep_phase_flops) per height and phase over the CUDA-event time, against the derived peak
     of the pipe each phase runs on (FP64; FP32 for the plain mixed finish; double-float: the FP32
     peak over the 15 FP32 instructions of one double-float multiply-add)."""
-    reduced = finish != "fp64"
-    flops = sweep_phase_flops(N, r, s, leaf, reduced)
+    flops = sweep_phase_flops(N, r, s, leaf, False if finish == "fp64" else finish)
     names = ("side", "bases", "D", "merge")
     pipe = {"side": "fp64", "bases": "fp32" if finish == "fp32" else "fp64",
             "D": finish, "merge": finish}
@@ -673,6 +692,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-config3", action="store_true",
                     help="skip the N = 65536 mixed-precision workload")
+    ap.add_argument("--no-apply", action="store_true",
+                    help="skip Algorithm 1 on the N = 2^22 exact-HBS operator")
     ap.add_argument("--workload", default="logkernel",
                     choices=["logkernel", "doublelayer", "scaling", "batched", "apply"],
                     help="logkernel: the timed N = 32768 log-kernel step (default); doublelayer: "
@@ -962,7 +983,8 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
-    if not args.only and args.workload == "logkernel" and (not args.no_batched or not args.no_config3):
+    if not args.only and args.workload == "logkernel" and (not args.no_batched or not args.no_config3
+                                                            or not args.no_apply):
         for rr in results.values():
             rr["h"].free()
         results = {}
@@ -972,6 +994,8 @@ def main():
             line["config3"] = run_config3(hb, torch, min(args.steps, 5), 3)
         if not args.no_batched:
             line["batched"] = run_batched(hb, torch)
+        if not args.no_apply:
+            line["apply"] = run_apply(hb, torch, logN=22, reps=3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, sample = oracle_sample_time(N, r, s, leaf, workload=args.workload)
         line["cpu_baseline"] = {"value": N * s / t_cpu, "unit": UNIT, "cores": cpu_cores(),

@@ -173,7 +173,9 @@ typedef struct hbs_handle hbs_handle;   /* opaque: owns the factors and all work
  * pushed through it in FP64; HBS_PREC_MIXED_BF16X3/X6 compute the bases, D_tau and the parent
  * blocks in FP32, HBS_PREC_MIXED_COMPENSATED the bases in FP64 and D_tau and the parent blocks
  * in double-float (factors stored in FP64). The D and merge tiles of the reduced finishes take
- * r (n + 1) + 3 n r + n (n + 1) + n^2 values (4-byte floats, or 8-byte pairs).
+ * r (n + 1) + 3 n r + n (n + 1) + n^2 values (4-byte floats, or 8-byte pairs); a tree height
+ * whose double-float tiles exceed 227 KB (n near 96 and above) runs D_tau and the merges in FP64
+ * instead.
  * Errors: HBS_ERR_ARG, HBS_ERR_SHAPE, HBS_ERR_UNSUPPORTED, HBS_ERR_NOMEM, HBS_ERR_CUDA.
  */
 int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out);

@@ -76,6 +76,9 @@ size_t side_smem_doubles(int n, int s);
 // The finish of a sweep (bases, D_tau, merges): FP64, FP32, or double-float (FP32 pairs).
 constexpr int kFinishF64 = 0, kFinishF32 = 1, kFinishDF32 = 2;
 size_t node_smem_bytes(int n, int r, int s, int finish);   // largest sweep-kernel tile
+// The finish a height with nodes of up to n rows runs (the double-float finish falls back to FP64
+// where its tiles exceed shared memory).
+int effective_finish(int n, int r, int finish);
 constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
 constexpr int kMaxSideCluster = 8;      // CTAs sharing one test-block factorization

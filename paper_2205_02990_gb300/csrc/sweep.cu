@@ -885,15 +885,27 @@ size_t merge_r_smem_reals(int n, int r, int chunk) {
          static_cast<size_t>(r) * chunk;
 }
 
+size_t finish_smem_bytes(int n, int r, int finish) {
+  if (finish == kFinishF32 || finish == kFinishDF32) {
+    const size_t w = finish == kFinishF32 ? sizeof(float) : sizeof(dfloat);
+    return std::max(dchain_smem_reals(n, r) * w, merge_r_smem_reals(n, r, kMergeCols) * w);
+  }
+  return std::max(dblk_smem_doubles(r, n) * sizeof(double), merge_smem_doubles(n) * sizeof(double));
+}
+
+// The finish a height of nodes of up to n rows runs: the double-float tiles of the one-CTA-per-
+// node D kernel grow as 8 (2 n^2 + 4 n r) bytes and pass 227 KB near n = 96; such heights run the
+// FP64 finish (spread over several CTAs per node), which is at least as accurate.
+int effective_finish(int n, int r, int finish) {
+  if (finish == kFinishDF32 && finish_smem_bytes(n, r, finish) > kMaxNodeSmemBytes) return kFinishF64;
+  return finish;
+}
+
 // The largest shared-memory tile the sweep kernels need for a node of n rows.
 size_t node_smem_bytes(int n, int r, int s, int finish) {
   const size_t d = sizeof(double);
   const size_t common = std::max(side_smem_doubles(n, s) * d, bases_smem_doubles(n, r) * d);
-  if (finish == kFinishF32 || finish == kFinishDF32) {
-    const size_t w = finish == kFinishF32 ? sizeof(float) : sizeof(dfloat);
-    return std::max({common, dchain_smem_reals(n, r) * w, merge_r_smem_reals(n, r, kMergeCols) * w});
-  }
-  return std::max({common, dblk_smem_doubles(r, n) * d, merge_smem_doubles(n) * d});
+  return std::max(common, finish_smem_bytes(n, r, effective_finish(n, r, finish)));
 }
 
 int side_row_splits(int ntasks, int n, int s) {
@@ -986,6 +998,7 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   if (ntasks <= 0) return cudaSuccess;
   auto mark = [&](int i) { return marks ? cudaEventRecord(marks[i], st) : cudaSuccess; };
   if (max_s > kMaxS) return cudaErrorInvalidValue;
+  finish = effective_finish(max_n, max_r, finish);
   const bool reduced = finish == kFinishF32 || finish == kFinishDF32;
   const size_t rsize = finish == kFinishF32 ? sizeof(float) : sizeof(dfloat);
   // about four merge CTAs per SM in all; chunks of 8 .. 32 columns

@@ -93,7 +93,10 @@ def _worst_factor(hb, h, F, blk, L, item=0):
 
 
 @pytest.mark.parametrize("N,r,s,leaf", [(2048, 40, 120, 64), (1024, 10, 30, 16), (777, 12, 40, 26),
-                                        (3000, 16, 48, 32), (129, 4, 12, 8)])
+                                        (3000, 16, 48, 32), (129, 4, 12, 8),
+                                        # upper nodes of 100 rows: their double-float tiles exceed
+                                        # shared memory, those heights run the FP64 finish
+                                        (4096, 50, 150, 64)])
 def test_compensated_sweep_random_inputs(hb, N, r, s, leaf):
     x = [gaussian((N, s), 7 * N + i) for i in range(4)]
     F, blk = ocompress(*x, r, leaf, keep_blocks=True)
