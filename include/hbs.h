@@ -227,8 +227,10 @@ int hbs_load_factors(hbs_handle* h, const void* src, void* cuda_stream);
  * Every shape rounds exactly alike, so the factors do not depend on the tuning.
  * hbs_autotune times R = 1, 2, 3, 4, 6, 8, 12, 16 and C = 1, 2, 3, 4, 6, 8 (at most n/8, and C only
  * where the cluster's shared-memory tile fits) on the handle's current inputs -- execute the
- * handle once first -- and keeps the fastest; it synchronizes cuda_stream and leaves the factors
- * unchanged. hbs_get_tuning returns the number of heights in *heights and copies up to `count`
+ * handle once first -- and keeps the fastest; then, per height, the grids of the finish kernels
+ * (the merges' column chunk, 8 .. 32, and for the FP64 finish the D kernels' column blocks per
+ * node, 1 .. 8), kept until the next hbs_autotune. It synchronizes cuda_stream and leaves the
+ * factors unchanged (every shape rounds alike). hbs_get_tuning returns the number of heights in *heights and copies up to `count`
  * values to R (may be NULL); hbs_set_tuning installs saved ones (values below -8 read as -8).
  * Errors: HBS_ERR_ARG, HBS_ERR_CUDA. */
 int hbs_autotune(hbs_handle* h, void* cuda_stream);

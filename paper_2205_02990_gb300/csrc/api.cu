@@ -88,6 +88,7 @@ struct Height {
   NodeTask* d_tasks = nullptr;
   int max_n = 0, max_r = 0, max_s = 0;
   int R = 0;                  // side-kernel row splits (0: automatic, > 0: tuned)
+  hbs::FinishShape fs;        // grids of the finish kernels (0: automatic)
 };
 
 }  // namespace
@@ -126,6 +127,7 @@ struct hbs_handle {
   std::vector<int> batch_sizes;
   int batch_ncols = 0;
   std::vector<int> tuned_R;   // per height, kept across task rebuilds
+  std::vector<hbs::FinishShape> tuned_fs;
   // the sweep's launches captured once per set of inputs and replayed
   bool use_graph = true;
   cudaGraphExec_t graph_exec = nullptr;
@@ -188,6 +190,7 @@ void build_tasks(hbs_handle* h) {
   for (auto& H : h->heights) cudaFree(H.d_tasks);
   h->heights.assign(maxL + 1, Height{});
   for (int t = 0; t <= maxL && t < int(h->tuned_R.size()); ++t) h->heights[t].R = h->tuned_R[t];
+  for (int t = 0; t <= maxL && t < int(h->tuned_fs.size()); ++t) h->heights[t].fs = h->tuned_fs[t];
   for (auto& it : h->items) {
     const int r = it.r, s = it.s;
     for (int level = it.L; level >= 0; --level) {
@@ -272,7 +275,7 @@ cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
   if (me != cudaSuccess) return me;
   for (auto& H : h->heights) {
     cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
-                                            H.max_s, finish, H.R, h->d_status, st);
+                                            H.max_s, finish, H.R, h->d_status, st, nullptr, H.fs);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1041,6 +1044,54 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  // The finish kernels' grids per height: the merge chunk, then (FP64 finish) the D column
+  // blocks, each timed over the D and merge launches of one run of the whole height (side,
+  // bases, D, merges: the height's outputs are recomputed from the same inputs, and every
+  // grid rounds alike, so the factors do not change).
+  cudaEvent_t ev[5];
+  int made = 0;
+  cudaError_t fe = cudaSuccess;
+  for (; made < 5 && fe == cudaSuccess; ++made) fe = cudaEventCreate(&ev[made]);
+  const int finish = finish_of(h->precision);
+  h->tuned_fs.assign(h->heights.size(), hbs::FinishShape{});
+  auto time_finish = [&](Height& H, hbs::FinishShape fs, float* ms) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)     // untimed, then timed
+      e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r, H.max_s,
+                                  finish, H.R, h->d_status, st, ev, fs);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ev[2], ev[4]);
+    return e;
+  };
+  for (size_t t = 0; t < h->heights.size() && fe == cudaSuccess; ++t) {
+    Height& H = h->heights[t];
+    if (H.tasks.size() == 1 && H.tasks[0].is_root) continue;   // the root has no finish
+    hbs::FinishShape best{};
+    float best_ms = 1e30f;
+    for (int chunk : {0, 8, 16, 32}) {
+      hbs::FinishShape fs = best;
+      fs.merge_chunk = chunk;
+      float ms = 0.f;
+      fe = time_finish(H, fs, &ms);
+      if (fe != cudaSuccess) break;
+      if (ms < best_ms) { best_ms = ms; best = fs; }
+    }
+    if (finish == hbs::kFinishF64 || hbs::effective_finish(H.max_n, H.max_r, finish) == hbs::kFinishF64) {
+      const hbs::FinishShape base = best;
+      for (int blocks : {1, 2, 4, 8}) {
+        if (fe != cudaSuccess) break;
+        hbs::FinishShape fs = base;
+        fs.d_blocks = blocks;
+        float ms = 0.f;
+        fe = time_finish(H, fs, &ms);
+        if (fe == cudaSuccess && ms < best_ms) { best_ms = ms; best = fs; }
+      }
+    }
+    H.fs = best;
+    h->tuned_fs[t] = best;
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  if (fe != cudaSuccess) return cuda_fail(fe, "hbs_autotune: finish shapes");
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;
@@ -1065,7 +1116,7 @@ int hbs_profile_sweep(hbs_handle* h, void* cuda_stream, float* ms, int32_t count
   for (size_t t = 0; t < h->heights.size() && e == cudaSuccess; ++t) {
     Height& H = h->heights[t];
     e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r, H.max_s, finish,
-                                H.R, h->d_status, st, ev);
+                                H.R, h->d_status, st, ev, H.fs);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
       float v = 0.f;

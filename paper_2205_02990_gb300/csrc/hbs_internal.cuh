@@ -83,12 +83,21 @@ constexpr size_t kMaxNodeSmemBytes = 227 * 1024;
 constexpr int kMaxS = 192;              // register tile of the sample-row streaming
 constexpr int kMaxSideCluster = 8;      // CTAs sharing one test-block factorization
 
+// Grids of the finish kernels of one height: merge_chunk = columns per merge CTA (8 .. 32),
+// d_blocks = column blocks per node of the FP64 D kernels (1 .. 8); 0 = the automatic choice
+// from the node count. Every choice rounds exactly alike.
+struct FinishShape {
+  int merge_chunk = 0;
+  int d_blocks = 0;
+};
+
 // One tree height of Algorithm 2: the side kernel (FP64), then the bases, D_tau and merge
 // kernels in the given finish precision. With marks (5 events), records them before the side
 // kernel and after the side, bases, D and merge launches.
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
                                int max_s, int finish, int row_splits, int* d_status,
-                               cudaStream_t st, cudaEvent_t* marks = nullptr);
+                               cudaStream_t st, cudaEvent_t* marks = nullptr,
+                               FinishShape shape = FinishShape{});
 // The side kernel of one height alone (for tuning; idempotent). R > 0: R row slices per
 // (node, side), each CTA factoring the test block; R < 0: a cluster of -R CTAs per (node, side)
 // sharing one factorization.

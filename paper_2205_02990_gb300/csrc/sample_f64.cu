@@ -294,16 +294,15 @@ cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, con
 cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, const double* Om,
                                    const double* Ps, int s, double* Y, double* Z,
                                    cudaStream_t st) {
-  // Row blocks (multiples of the 64-row tile) growing from ~N/64 rows by half each time up to
-  // ~N/8 rows (at most 2 GiB of staging each): the first copy, which nothing hides, stays short,
-  // and while the blocks grow each block's products still outlast the next block's copy
-  // whenever the host link carries more than ~2/3 of what the products consume.
+  // Row blocks (multiples of the 64-row tile) doubling from ~N/32 rows up to ~N/8 rows (at most
+  // 2 GiB of staging each): the first copy, which nothing hides, stays short, and few blocks are
+  // small (a small block's products fill the GPU less well).
   const int64_t cap = std::max<int64_t>(BM, (int64_t(1) << 28) / std::max<int64_t>(1, N) / BM * BM);
   const int64_t nb_max = std::min(N, std::max<int64_t>(BM, std::min(((N + 7) / 8 + BM - 1) / BM * BM, cap)));
   std::vector<int64_t> rows_of;
   std::vector<int> zs_of;
   int64_t total_slices = 0;
-  for (int64_t r0 = 0, nb = std::min(nb_max, ((N + 63) / 64 + BM - 1) / BM * BM); r0 < N;) {
+  for (int64_t r0 = 0, nb = std::min(nb_max, ((N + 31) / 32 + BM - 1) / BM * BM); r0 < N;) {
     const int64_t rows = std::min(nb, N - r0);
     int zs = 0;                                        // Z slices of this block
     int64_t zk = 0;
@@ -312,7 +311,7 @@ cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, cons
     zs_of.push_back(zs);
     total_slices += zs;
     r0 += rows;
-    nb = std::min(nb_max, (nb + nb / 2 + BM - 1) / BM * BM);
+    nb = std::min(nb_max, 2 * nb);
   }
   const int64_t count = N * s;
   HostStream* h = nullptr;
@@ -327,9 +326,12 @@ cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, cons
     const int64_t rows = rows_of[b];
     const int zs = zs_of[b];
     if (b >= 2) e = cudaStreamWaitEvent(h->copy, h->consumed[slot], 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(h->stage[slot], N * sizeof(double), A + r0 * lda, lda * sizeof(double),
-                            N * sizeof(double), rows, cudaMemcpyHostToDevice, h->copy);
+    if (e == cudaSuccess)                              // contiguous rows: one 1D copy
+      e = lda == N ? cudaMemcpyAsync(h->stage[slot], A + r0 * lda, rows * N * sizeof(double),
+                                     cudaMemcpyHostToDevice, h->copy)
+                   : cudaMemcpy2DAsync(h->stage[slot], N * sizeof(double), A + r0 * lda,
+                                       lda * sizeof(double), N * sizeof(double), rows,
+                                       cudaMemcpyHostToDevice, h->copy);
     if (e == cudaSuccess) e = cudaEventRecord(h->copied[slot], h->copy);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->copied[slot], 0);
     if (e == cudaSuccess) e = product(false, h->stage[slot], N, rows, N, Om, s, Y + r0 * s, st);

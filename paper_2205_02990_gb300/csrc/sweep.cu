@@ -994,20 +994,21 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
 
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
                                int max_s, int finish, int row_splits, int* d_status,
-                               cudaStream_t st, cudaEvent_t* marks) {
+                               cudaStream_t st, cudaEvent_t* marks, FinishShape shape) {
   if (ntasks <= 0) return cudaSuccess;
   auto mark = [&](int i) { return marks ? cudaEventRecord(marks[i], st) : cudaSuccess; };
   if (max_s > kMaxS) return cudaErrorInvalidValue;
   finish = effective_finish(max_n, max_r, finish);
   const bool reduced = finish == kFinishF32 || finish == kFinishDF32;
   const size_t rsize = finish == kFinishF32 ? sizeof(float) : sizeof(dfloat);
-  // about four merge CTAs per SM in all; chunks of 8 .. 32 columns
+  // automatic: about four merge CTAs per SM in all; chunks of 8 .. 32 columns
   const int want = std::max(1, (4 * 152) / (2 * ntasks));
-  const int chunk = std::max(8, std::min(kMergeCols, (max_s + want - 1) / want));
+  const int chunk = shape.merge_chunk > 0 ? std::max(8, std::min(kMergeCols, shape.merge_chunk))
+                                          : std::max(8, std::min(kMergeCols, (max_s + want - 1) / want));
   const size_t side_bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
   const size_t bases_bytes = bases_smem_doubles(max_n, max_r) *
                              (finish == kFinishF32 ? sizeof(float) : sizeof(double));
-  const int blocks = dblk_blocks(ntasks);
+  const int blocks = shape.d_blocks > 0 ? std::min(8, shape.d_blocks) : dblk_blocks(ntasks);
   const int nb = (max_n + blocks - 1) / blocks;
   const size_t dblk_bytes = reduced ? dchain_smem_reals(max_n, max_r) * rsize
                                     : dblk_smem_doubles(max_r, nb) * sizeof(double);

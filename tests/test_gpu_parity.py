@@ -340,3 +340,25 @@ def test_full_size_tree_every_factor_matches_oracle(hb):
     worst, where = factor_errors(hb, h, F, blk, range(1, 2 ** (F.L + 1)))
     assert worst <= 1e-10, (worst, where)
     h.free()
+
+
+@pytest.mark.parametrize("precision", [0, 2, 4])
+def test_autotune_keeps_factors_bit_identical(hb, precision):
+    # hbs_autotune picks the side shape and the finish kernels' grids (merge chunk, D column
+    # blocks) per height; every choice rounds alike, so the factors after a tuned execution are
+    # bit-identical to the automatic ones
+    N, r, s, leaf = 4096, 40, 120, 64
+    x = [dev(gaussian((N, s), 70 + i)) for i in range(4)]
+    h = hb.hbs_plan([hb.Problem(N, r, s, leaf, *x)], precision=precision)
+    hb.hbs_execute(h)
+    hb.hbs_sync_status(h)
+    before = torch.empty(hb.hbs_factor_bytes(h) // 8, dtype=torch.float64, device="cuda")
+    hb.hbs_copy_factors(h, before)
+    hb.hbs_autotune(h)
+    hb.hbs_execute(h)
+    hb.hbs_sync_status(h)
+    after = torch.empty_like(before)
+    hb.hbs_copy_factors(h, after)
+    torch.cuda.synchronize()
+    assert torch.equal(before, after)
+    h.free()
