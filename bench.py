@@ -364,8 +364,9 @@ MODES = {
                       "(28 FP16 digit-pair products on tcgen05 tensor cores, exact FP32 sums); "
                       "FP64 sweep"),
     "cmp": dict(sample=4, sweep=4, a="f64",
-                what="A stored FP64; products from 5 exact 8-bit digits per entry (15 FP16 "
-                     "digit-pair products on tcgen05 tensor cores, exact FP32 sums); sweep with "
+                what="A stored FP64; products from 5 exact 8-bit digits per entry, one exponent "
+                     "per 64 x 64 block of A (15 FP16 digit-pair products on tcgen05 tensor cores, "
+                     "exact FP32 sums); sweep with "
                      "FP64 nullspace LQ / pseudo-inverse and bases, double-float (compensated "
                      "FP32) D_tau and merges"),
     "mixed3": dict(sample=1, sweep=1, a="f32",
@@ -920,7 +921,8 @@ def main():
         pairs = 28 if MODES[head]["sample"] == 3 else 15
         peak = BF16_TFLOPS_SUSTAINED
         achieved = pairs * flops_product / res["per_launch"] / 1e12
-        roofline = {"kernel": f"digit products per FP64 product (oz_split_a/b + oz_gemm + oz_reduce; "
+        split = "oz_split_a" if pairs == 28 else "oz_split_shared"
+        roofline = {"kernel": f"digit products per FP64 product ({split}, oz_split_b, oz_gemm, oz_reduce; "
                               f"{pairs} exact FP16 digit-pair products)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,

@@ -68,8 +68,12 @@ typedef enum {
                                scratch (the digit planes of A in both orientations) */
   HBS_PREC_MIXED_COMPENSATED = 4
                             /* sampling: as HBS_PREC_FP64_TC with 5 digits per entry (15
-                               digit-pair products, terms to ~2^-38 of the block maxima; needs
-                               about 20 N^2 bytes of scratch). Sweep: the LQ of each test block
+                               digit-pair products) and one exponent per 64 x 64 block of A, its
+                               digit planes kept in one orientation (the product with A^* reads
+                               them transposed): each entry is kept to ~2^-38 of the largest
+                               entry of its block, so a row or column far below the rest of its
+                               block loses relative accuracy (the products' normwise error is
+                               unaffected); about 10 N^2 bytes of scratch. Sweep: the LQ of each test block
                                (nullspace, pseudo-inverse) and the bases in FP64, D_tau and the
                                parent blocks in double-float arithmetic (pairs of FP32 numbers,
                                ~48 significant bits, FP32 exponent range: every intermediate
@@ -190,6 +194,28 @@ int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream);
 /* hbs_plan followed by hbs_execute. */
 int hbs_compress(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_handle** out,
                  void* cuda_stream);
+
+/* Algorithm 2 from the operator on, for a handle planned for one problem: hbs_sample into
+ * probs->Omega, Psi, Y, Z (draws from `seed`, products at `precision`), then hbs_execute, with
+ * the leaves' test-block factorizations overlapped with the products. The LQ of each leaf's
+ * Omega_tau and Psi_tau (Section 2.4) needs only the test matrices -- the remark of Section 1
+ * that the test matrices can be drawn, and all work that depends on them alone be done, before
+ * the operator is applied once -- so it runs on a second stream owned by the handle (highest
+ * stream priority) from the draws on, and `cuda_stream` waits for it before the sweep. The
+ * leaf level's side kernel then takes those factorizations instead of computing them: the
+ * factors are bit-identical to hbs_sample + hbs_execute. Where the leaf height runs the cluster
+ * form of the side kernel (a tree with few leaves) nothing is overlapped.
+ * probs->Omega, Psi, Y and Z are written (writable device buffers, N x s FP64 row-major).
+ * op->N must equal probs->N; the operator rules are hbs_sample's. The handle's second stream
+ * and its image buffer (2 leaves (n (s + 1) + 2 n) doubles for leaves of n rows) are made on
+ * the first call; a later call must be ordered after the earlier one's sweep (the same stream,
+ * or the caller's synchronization). A call made while `cuda_stream` is being captured records
+ * the fork and join into the capture.
+ * Errors: those of hbs_sample and hbs_execute; HBS_ERR_ARG when the handle holds more than one
+ * problem; HBS_ERR_NOMEM.
+ */
+int hbs_sample_execute(hbs_handle* h, const hbs_operator* op, uint64_t seed, int32_t precision,
+                       const hbs_problem* probs, void* cuda_stream);
 
 /* Algorithm 1: Out = A~ X (trans = 0) or A~^* X (trans = 1) for the compressed form of problem
  * `item` of the handle. X, Out: device, FP64, row-major N x ncols, leading dimension ncols,

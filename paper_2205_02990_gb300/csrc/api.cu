@@ -128,10 +128,18 @@ struct hbs_handle {
   int batch_ncols = 0;
   std::vector<int> tuned_R;   // per height, kept across task rebuilds
   std::vector<hbs::FinishShape> tuned_fs;
-  // the sweep's launches captured once per set of inputs and replayed
+  // the sweep's launches captured once per set of inputs and replayed; graph_pre: the same
+  // with the leaves' test blocks factored beforehand (hbs_sample_execute)
   bool use_graph = true;
   cudaGraphExec_t graph_exec = nullptr;
+  cudaGraphExec_t graph_pre = nullptr;
   cudaStream_t capture_stream = nullptr;
+  // hbs_sample_execute: the leaves' LQ images, the stream they are made on (while the products
+  // run on the caller's stream) and the events joining the two
+  double* lq_buf = nullptr;
+  size_t lq_doubles = 0;
+  cudaStream_t lq_stream = nullptr;
+  cudaEvent_t ev_drawn = nullptr, ev_lq = nullptr;
   // hbs_apply_batch workspace and task list
   double* batch_ws = nullptr;
   size_t batch_ws_doubles = 0;
@@ -262,20 +270,36 @@ void free_handle(hbs_handle* h) {
   cudaFree(h->batch_ws);
   cudaFree(h->d_batch);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph_pre) cudaGraphExecDestroy(h->graph_pre);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  cudaFree(h->lq_buf);
+  if (h->lq_stream) cudaStreamDestroy(h->lq_stream);
+  if (h->ev_drawn) cudaEventDestroy(h->ev_drawn);
+  if (h->ev_lq) cudaEventDestroy(h->ev_lq);
   delete h;
 }
 
-// The sweep's launches, one launch_sweep_level per height, finest height first.
-cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
+// The captured sweeps are stale once the tasks, the shapes or the graph setting change.
+void drop_graphs(hbs_handle* h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph_pre) cudaGraphExecDestroy(h->graph_pre);
+  h->graph_exec = nullptr;
+  h->graph_pre = nullptr;
+}
+
+// The sweep's launches, one launch_sweep_level per height, finest height first; with pre, the
+// leaf height's side kernel takes the factorizations in lq_buf.
+cudaError_t launch_levels(hbs_handle* h, cudaStream_t st, bool pre = false) {
   const int finish = finish_of(h->precision);
   // a new run: clear the abort flag an earlier run may have left (the report bits stay until
   // hbs_sync_status reads them)
   cudaError_t me = cudaMemsetAsync(h->d_status + hbs::kAbortWord, 0, sizeof(int), st);
   if (me != cudaSuccess) return me;
-  for (auto& H : h->heights) {
+  for (size_t t = 0; t < h->heights.size(); ++t) {
+    const Height& H = h->heights[t];
     cudaError_t e = hbs::launch_sweep_level(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_r,
-                                            H.max_s, finish, H.R, h->d_status, st, nullptr, H.fs);
+                                            H.max_s, finish, H.R, h->d_status, st, nullptr, H.fs,
+                                            (pre && t == 0) ? h->lq_buf : nullptr);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -284,15 +308,16 @@ cudaError_t launch_levels(hbs_handle* h, cudaStream_t st) {
 // Runs the sweep on `st`: replays the captured graph when there is one, else captures the
 // launches on a private stream (so a caller's own capture of `st` is never disturbed) and
 // replays that; launches directly when `st` is itself being captured or capture fails.
-int launch_sweep(hbs_handle* h, cudaStream_t st) {
+int launch_sweep(hbs_handle* h, cudaStream_t st, bool pre = false) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(st, &cs);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
   if (!h->use_graph || cs != cudaStreamCaptureStatusNone) {
-    e = launch_levels(h, st);
+    e = launch_levels(h, st, pre);
     return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep kernels");
   }
-  if (!h->graph_exec) {
+  cudaGraphExec_t& exec = pre ? h->graph_pre : h->graph_exec;
+  if (!exec) {
     if (!h->capture_stream &&
         cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
       h->capture_stream = nullptr;
@@ -301,11 +326,11 @@ int launch_sweep(hbs_handle* h, cudaStream_t st) {
     cudaGraph_t graph = nullptr;
     if (h->use_graph &&
         cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const cudaError_t le = launch_levels(h, h->capture_stream);
+      const cudaError_t le = launch_levels(h, h->capture_stream, pre);
       const cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &graph);
       if (le != cudaSuccess || ce != cudaSuccess ||
-          cudaGraphInstantiate(&h->graph_exec, graph, 0) != cudaSuccess) {
-        h->graph_exec = nullptr;
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        exec = nullptr;
         h->use_graph = false;
         cudaGetLastError();                       // clear a sticky launch error from capture
       }
@@ -314,12 +339,12 @@ int launch_sweep(hbs_handle* h, cudaStream_t st) {
       h->use_graph = false;
       cudaGetLastError();
     }
-    if (!h->graph_exec) {
-      e = launch_levels(h, st);
+    if (!exec) {
+      e = launch_levels(h, st, pre);
       return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep kernels");
     }
   }
-  e = cudaGraphLaunch(h->graph_exec, st);
+  e = cudaGraphLaunch(exec, st);
   return e == cudaSuccess ? HBS_OK : cuda_fail(e, "sweep graph launch");
 }
 
@@ -487,8 +512,10 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
       return (v && atoi(v) == 4) ? 4 : 5;
     }();
     const int digits = precision == HBS_PREC_FP64_TC ? digits64 : digits_mixed;
+    // compensated products: one exponent per 64 x 64 block of A, planes in one orientation
     cudaError_t e = hbs::launch_sample_dense_oz(static_cast<const double*>(op->A), op->lda, op->N,
-                                                Omega, Psi, s, Y, Z, digits, st);
+                                                Omega, Psi, s, Y, Z, digits,
+                                                precision == HBS_PREC_MIXED_COMPENSATED, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core digit sampling");
     return ok();
   }
@@ -659,35 +686,133 @@ int hbs_plan(int32_t batch, const hbs_problem* probs, int32_t precision, hbs_han
   return ok();
 }
 
-int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream) {
-  if (!h || !probs) return fail(HBS_ERR_ARG, "hbs_execute: NULL argument");
-  if (check_device(h, "hbs_execute") != HBS_OK) return HBS_ERR_ARG;
+namespace {
+
+// Checks probs against the plan and points the tasks at its blocks (rebuilt and uploaded on st
+// when a pointer changed).
+int bind_problems(hbs_handle* h, const hbs_problem* probs, cudaStream_t st, const char* who) {
   bool changed = !h->tasks_uploaded;
   for (size_t i = 0; i < h->items.size(); ++i) {
     Item& it = h->items[i];
     const hbs_problem& p = probs[i];
     if (p.N != it.N || p.r != it.r || p.s != it.s || p.leaf_max != it.leaf_max)
-      return fail(HBS_ERR_ARG, "hbs_execute: problem %zu differs from the plan", i);
+      return fail(HBS_ERR_ARG, "%s: problem %zu differs from the plan", who, i);
     if (!p.Omega || !p.Psi || !p.Y || !p.Z)
-      return fail(HBS_ERR_ARG, "hbs_execute: problem %zu has a NULL input", i);
+      return fail(HBS_ERR_ARG, "%s: problem %zu has a NULL input", who, i);
     if (p.Omega != it.Om || p.Psi != it.Ps || p.Y != it.Y || p.Z != it.Z) changed = true;
     it.Om = p.Omega;
     it.Ps = p.Psi;
     it.Y = p.Y;
     it.Z = p.Z;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (changed) {
     build_tasks(h);
     const int rc = upload_tasks(h, st);
     if (rc != HBS_OK) return rc;
     h->tasks_uploaded = true;
+    drop_graphs(h);
   }
-  if (changed && h->graph_exec) {
-    cudaGraphExecDestroy(h->graph_exec);
-    h->graph_exec = nullptr;
+  return HBS_OK;
+}
+
+// The leaf height can take its factorizations from node_lq when it runs the one-CTA side form.
+bool leaves_prefactorable(const hbs_handle* h) {
+  if (h->items.size() != 1 || h->items[0].L < 1 || h->heights.empty()) return false;
+  const Height& H = h->heights[0];
+  return hbs::side_shape(int(H.tasks.size()), H.max_n, H.max_s, H.R) > 0;
+}
+
+// lq_buf, the second stream (the highest priority, so that its CTAs are placed among the
+// products' as SMs free up) and the two events, made on first use.
+int ensure_lq_resources(hbs_handle* h) {
+  const Height& H = h->heights[0];
+  const size_t need = size_t(2) * H.tasks.size() * size_t(hbs::side_lq_stride(H.max_n, H.max_s));
+  if (need > h->lq_doubles) {
+    cudaFree(h->lq_buf);
+    h->lq_buf = nullptr;
+    h->lq_doubles = 0;
+    drop_graphs(h);                                    // graph_pre holds the old address
+    cudaError_t e = cudaMalloc(&h->lq_buf, need * sizeof(double));
+    if (e != cudaSuccess) return fail(HBS_ERR_NOMEM, "leaf LQ images: %s", cudaGetErrorString(e));
+    h->lq_doubles = need;
   }
-  const int rc = launch_sweep(h, st);
+  if (!h->lq_stream) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&h->lq_stream, cudaStreamNonBlocking, greatest);
+    if (e != cudaSuccess) {
+      h->lq_stream = nullptr;
+      return cuda_fail(e, "leaf LQ stream");
+    }
+  }
+  for (cudaEvent_t* ev : {&h->ev_drawn, &h->ev_lq}) {
+    if (!*ev) {
+      cudaError_t e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        *ev = nullptr;
+        return cuda_fail(e, "leaf LQ event");
+      }
+    }
+  }
+  return HBS_OK;
+}
+
+}  // namespace
+
+int hbs_execute(hbs_handle* h, const hbs_problem* probs, void* cuda_stream) {
+  if (!h || !probs) return fail(HBS_ERR_ARG, "hbs_execute: NULL argument");
+  if (check_device(h, "hbs_execute") != HBS_OK) return HBS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int rc = bind_problems(h, probs, st, "hbs_execute");
+  if (rc != HBS_OK) return rc;
+  rc = launch_sweep(h, st);
+  if (rc != HBS_OK) return rc;
+  return ok();
+}
+
+int hbs_sample_execute(hbs_handle* h, const hbs_operator* op, uint64_t seed, int32_t precision,
+                       const hbs_problem* probs, void* cuda_stream) {
+  if (!h || !probs || !op) return fail(HBS_ERR_ARG, "hbs_sample_execute: NULL argument");
+  if (h->items.size() != 1)
+    return fail(HBS_ERR_ARG, "hbs_sample_execute: the handle must hold one problem");
+  if (check_device(h, "hbs_sample_execute") != HBS_OK) return HBS_ERR_ARG;
+  const hbs_problem& p = probs[0];
+  if (op->N != p.N) return fail(HBS_ERR_ARG, "hbs_sample_execute: operator N differs from the problem's");
+  int rc = check_operator(op, p.s, precision, p.Omega, p.Psi, p.Y, p.Z, "hbs_sample_execute");
+  if (rc != HBS_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  rc = bind_problems(h, probs, st, "hbs_sample_execute");
+  if (rc != HBS_OK) return rc;
+  // the problem's blocks are the sweep's inputs (const there); here they are written
+  double* Om = const_cast<double*>(p.Omega);
+  double* Ps = const_cast<double*>(p.Psi);
+  double* Y = const_cast<double*>(p.Y);
+  double* Z = const_cast<double*>(p.Z);
+  const int64_t count = p.N * int64_t(p.s);
+  cudaError_t e = hbs::launch_gaussian(count, 0u, seed, Om, st);
+  if (e == cudaSuccess) e = hbs::launch_gaussian(count, 1u, seed, Ps, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gaussian kernel");
+  const bool pre = leaves_prefactorable(h);
+  if (pre) {
+    rc = ensure_lq_resources(h);
+    if (rc != HBS_OK) return rc;
+    const Height& H = h->heights[0];
+    e = cudaEventRecord(h->ev_drawn, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->lq_stream, h->ev_drawn, 0);
+    if (e == cudaSuccess)
+      e = hbs::launch_side_lq(H.d_tasks, int(H.tasks.size()), H.max_n, H.max_s, h->lq_buf,
+                              h->d_status, h->lq_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_lq, h->lq_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "leaf LQ");
+  }
+  rc = hbs_sample_products(op, p.s, precision, Om, Ps, Y, Z, cuda_stream);
+  if (pre) {                                         // join the second stream in every case
+    e = cudaStreamWaitEvent(st, h->ev_lq, 0);
+    if (e != cudaSuccess && rc == HBS_OK) rc = cuda_fail(e, "leaf LQ join");
+  }
+  if (rc != HBS_OK) return rc;
+  rc = launch_sweep(h, st, pre);
   if (rc != HBS_OK) return rc;
   return ok();
 }
@@ -1092,10 +1217,7 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
   }
   for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
   if (fe != cudaSuccess) return cuda_fail(fe, "hbs_autotune: finish shapes");
-  if (h->graph_exec) {
-    cudaGraphExecDestroy(h->graph_exec);
-    h->graph_exec = nullptr;
-  }
+  drop_graphs(h);
   return ok();
 }
 
@@ -1141,20 +1263,14 @@ int hbs_set_tuning(hbs_handle* h, const int32_t* R, int32_t count) {
   h->tuned_R.assign(R, R + count);
   for (int t = 0; t < count && t < int(h->heights.size()); ++t)
     h->heights[t].R = std::max(-hbs::kMaxSideCluster, R[t]);
-  if (h->graph_exec) {
-    cudaGraphExecDestroy(h->graph_exec);
-    h->graph_exec = nullptr;
-  }
+  drop_graphs(h);
   return ok();
 }
 
 int hbs_set_graph(hbs_handle* h, int enable) {
   if (!h) return fail(HBS_ERR_ARG, "hbs_set_graph: NULL handle");
   h->use_graph = enable != 0;
-  if (h->graph_exec) {
-    cudaGraphExecDestroy(h->graph_exec);
-    h->graph_exec = nullptr;
-  }
+  drop_graphs(h);
   return ok();
 }
 

@@ -93,18 +93,27 @@ struct FinishShape {
 
 // One tree height of Algorithm 2: the side kernel (FP64), then the bases, D_tau and merge
 // kernels in the given finish precision. With marks (5 events), records them before the side
-// kernel and after the side, bases, D and merge launches.
+// kernel and after the side, bases, D and merge launches. With lq (a height whose side shape
+// is R > 0), the side kernel takes the test blocks' factorizations from launch_side_lq's output
+// instead of computing them.
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
                                int max_s, int finish, int row_splits, int* d_status,
                                cudaStream_t st, cudaEvent_t* marks = nullptr,
-                               FinishShape shape = FinishShape{});
+                               FinishShape shape = FinishShape{}, const double* lq = nullptr);
 // The side kernel of one height alone (for tuning; idempotent). R > 0: R row slices per
-// (node, side), each CTA factoring the test block; R < 0: a cluster of -R CTAs per (node, side)
-// sharing one factorization.
+// (node, side), each CTA factoring the test block (or copying it from lq); R < 0: a cluster of
+// -R CTAs per (node, side) sharing one factorization.
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
-                             int R, int* d_status, cudaStream_t st);
+                             int R, int* d_status, cudaStream_t st, const double* lq = nullptr);
+// The LQ of every test block of a height (both sides), written to lq: 2 ntasks images of
+// side_lq_stride(max_n, max_s) doubles, (node, side) at (2 node + side) * stride.
+cudaError_t launch_side_lq(const NodeTask* d_tasks, int ntasks, int max_n, int max_s, double* lq,
+                           int* d_status, cudaStream_t st);
+int64_t side_lq_stride(int max_n, int max_s);
 bool side_cluster_fits(int n, int s, int C);
 int side_row_splits(int ntasks, int n, int s);   // the automatic side shape (R as above)
+// The side shape a height runs: row_splits when set (tuned), else the automatic one.
+int side_shape(int ntasks, int n, int s, int row_splits);
 cudaError_t launch_gaussian(int64_t count, uint32_t stream_id, uint64_t seed, double* out,
                             cudaStream_t st);
 cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, const double* Om,
@@ -131,9 +140,11 @@ void column_tiles(int s, int* BN, int* BNt);
 // FP64-class sampling by exact bfloat16 digit products on the tensor cores (sample_oz.cu):
 // A FP64 row-major (any lda >= N), digits = 4 .. 7, s <= 256, N <= 2^20. The scratch it grows
 // holds the device status word at its start.
+// shared_planes: one exponent per 64 x 64 block of A and its digit planes in one orientation,
+// read transposed by the product with A^* (half the split's work and scratch).
 cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, const double* Om,
                                    const double* Ps, int s, double* Y, double* Z, int digits,
-                                   cudaStream_t st);
+                                   bool shared_planes, cudaStream_t st);
 cudaError_t sample_oz_status(int* host_status, bool clear);
 cudaError_t sample_oz_inject(int bits);
 // ncols: the column count of every task (1 .. 4 takes the grouped skinny kernel), or 0 when each

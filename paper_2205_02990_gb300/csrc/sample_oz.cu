@@ -265,6 +265,55 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// One 64 x 64 block of A with a single exponent for the whole block: the digit planes of A in
+// row-major order only (the product with A^* reads them transposed, an MN-major operand), and
+// that exponent as the per-row (EY) and per-column (EZ) exponents of the block. Half the
+// digit work of oz_split_a; entries far below their block's largest lose the corresponding
+// low bits (used with 5 digits, whose products are not FP64-class anyway).
+template <int S>
+__global__ void __launch_bounds__(256)
+    oz_split_shared(const double* __restrict__ A, int64_t lda, int64_t N, uint16_t* __restrict__ Yd,
+                    int64_t ldd, int16_t* __restrict__ EY, int16_t* __restrict__ EZ, int W,
+                    int* status) {
+  __shared__ double tile[64][65];
+  __shared__ int wexp[8];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 64, c0 = static_cast<int64_t>(blockIdx.x) * 64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = warp * 8 + rr;
+    const int64_t gr = r0 + r;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gc = c0 + lane + 32 * h;
+      tile[r][lane + 32 * h] = (gr < N && gc < N) ? A[gr * lda + gc] : 0.0;
+    }
+  }
+  __syncthreads();
+  int Em = kNoExp;                                     // the block's exponent: the largest row's
+#pragma unroll 1
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = warp * 8 + rr;
+    Em = max(Em, pair_block_exponent(tile[r][2 * lane], tile[r][2 * lane + 1], status));
+  }
+  if (lane == 0) wexp[warp] = Em;
+  __syncthreads();
+  int E = wexp[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) E = max(E, wexp[w]);
+  const size_t plane = static_cast<size_t>(N) * ldd;
+#pragma unroll 1
+  for (int rr = 0; rr < 8; ++rr) {
+    const int r = warp * 8 + rr;
+    if (r0 + r >= N) continue;
+    if (lane == 0) EY[(r0 + r) * W + blockIdx.x] = static_cast<int16_t>(E);
+    store_digit_pair<S>(tile[r][2 * lane], tile[r][2 * lane + 1], E, Yd + (r0 + r) * ldd + c0 + 2 * lane,
+                        plane);
+  }
+  if (threadIdx.x < 64 && c0 + threadIdx.x < N)
+    EZ[(c0 + threadIdx.x) * W + blockIdx.y] = static_cast<int16_t>(E);
+}
+
 // One 64-row window of a test matrix X (N x s, row-major): its exponent and the digit planes of
 // X^* (S x BNt rows of ldd entries; rows c >= s are zero).
 template <int S>
@@ -314,6 +363,7 @@ struct OzArgs {
   int W;               // 64-wide windows of the reduction
   int BN, BNt;         // columns per CTA tile; padded columns of the product
   int wchunk;          // windows per reduction split (<= kMaxWindowsPerSplit)
+  int slots;           // digit slots of the shared-memory ring (S .. kMaxSlots)
   const int16_t* EA;   // [M][W] exponent of row m of op(A) over window w
   const int16_t* EB;   // [W] exponent of the test matrix over window w
   float2* partial;     // [splits][M][BNt] (hi, lo), in units of 2^rexp
@@ -322,6 +372,7 @@ struct OzArgs {
 };
 
 constexpr int kAccBufs = 4;          // accumulators in tensor memory, 128 columns each
+constexpr int kMaxSlots = 11;        // digit slots: 2 mbarriers each in the 256-byte barrier area
 // Diagonals added to the running sum by TwoSum (hi exact, its rounding error into lo); the later
 // ones weigh < 2^-8 kExactDiags of diagonal 0 and go into lo with one FMA. FP64-class products
 // (S >= 6) take 4 (later terms < 2^-32 of the sum, each rounded to 2^-56 of it); the 5-digit
@@ -368,13 +419,14 @@ __device__ __forceinline__ void mma_f16_c(uint32_t tmem_d, uint64_t adesc, uint6
 }
 
 // The MMAs of diagonal D: pairs (i, D - i), four K = 16 steps each; on the last diagonal in
-// groups (k, S-1-k), (S-1-k, k), each group committed to freed[k] so that the producer can refill
-// those digits while the rest of the window runs. Fully unrolled with the descriptors of the
-// digit tiles precomputed, so that the single issuing thread spends few instructions per MMA.
-template <int S, int D>
+// groups (k, S-1-k), (S-1-k, k), each group committed to the slots of digits k and S-1-k
+// (freed[.]) so that the producer can refill them while the rest of the window runs. Fully
+// unrolled with the descriptors of the digit tiles precomputed per window, so that the single
+// issuing thread spends few instructions per MMA.
+template <int S, int D, int ASTEP>
 __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad)[S],
                                                const uint64_t (&bd)[S], uint32_t idesc,
-                                               uint64_t* freed) {
+                                               uint64_t* (&freed)[S]) {
   if constexpr (D >= S) {
     return;                                             // no such diagonal (never called)
   } else if constexpr (D < S - 1) {
@@ -382,8 +434,8 @@ __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad
     for (int i = 0; i <= D; ++i)
 #pragma unroll
       for (int kk = 0; kk < OBK / 16; ++kk) {
-        if (i == 0 && kk == 0) mma_f16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
-        else mma_f16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+        if (i == 0 && kk == 0) mma_f16_c<false>(acc, ad[i] + ASTEP * kk, bd[D - i] + 2 * kk, idesc);
+        else mma_f16_c<true>(acc, ad[i] + ASTEP * kk, bd[D - i] + 2 * kk, idesc);
       }
   } else {
     constexpr int G = (S + 1) / 2;
@@ -395,11 +447,12 @@ __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad
         if (t == 1 && i == k) continue;
 #pragma unroll
         for (int kk = 0; kk < OBK / 16; ++kk) {
-          if (k == 0 && t == 0 && kk == 0) mma_f16_c<false>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
-          else mma_f16_c<true>(acc, ad[i] + 2 * kk, bd[D - i] + 2 * kk, idesc);
+          if (k == 0 && t == 0 && kk == 0) mma_f16_c<false>(acc, ad[i] + ASTEP * kk, bd[D - i] + 2 * kk, idesc);
+          else mma_f16_c<true>(acc, ad[i] + ASTEP * kk, bd[D - i] + 2 * kk, idesc);
         }
       }
-      mma_commit(&freed[k]);
+      mma_commit(freed[k]);                             // digits k and S-1-k: their last use
+      if (S - 1 - k != k) mma_commit(freed[S - 1 - k]);
     }
   }
 }
@@ -408,7 +461,12 @@ __device__ __forceinline__ void issue_diagonal(uint32_t acc, const uint64_t (&ad
 // chunks c = part + P cc of the BN columns (part = (w - 2) / 4, P = drain warps / 4); its running
 // sums stay in registers. The drain shares each scheduler with the producer or the MMA thread,
 // whose issue slots must not be crowded out, so it stays at two warps per scheduler.
-template <int S>
+// MN = true: the A operand is read transposed from row-major digit planes of A (Z = A^* Psi
+// from the planes of A itself): each 128 x 64 digit tile is two TMA boxes of 64 reduction rows
+// x 64 output columns (128-byte swizzled rows), an MN-major operand (instruction descriptor bit
+// 15) whose two 64-column atoms lie 8 KB apart (leading byte offset) with 8-row groups 1 KB
+// apart (stride byte offset); a K = 16 step advances 16 rows = 2 KB.
+template <int S, bool MN = false>
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             OzArgs a) {
@@ -417,12 +475,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
   const int BN = a.BN;
   const int tile_b = BN * 128;
-  uint8_t* opA = smem;                                   // S digit tiles of A
-  uint8_t* opB = opA + S * kDigitTileA;                  // S digit tiles of the test matrix
-  constexpr int G = (S + 1) / 2;                         // digit groups {k, S-1-k}
-  uint64_t* full = reinterpret_cast<uint64_t*>(opB + S * tile_b);   // S: digit i landed
-  uint64_t* freed = full + S;                            // G: group k's last MMAs are done
-  uint64_t* acc_full = freed + G;                        // kAccBufs
+  const int NS = a.slots;                                // ring of digit slots (>= S)
+  uint8_t* opA = smem;                                   // NS digit tiles of A
+  uint8_t* opB = opA + NS * kDigitTileA;                 // NS digit tiles of the test matrix
+  uint64_t* full = reinterpret_cast<uint64_t*>(opB + NS * tile_b);  // NS: slot's tiles landed
+  uint64_t* empty = full + NS;                           // NS: slot's last MMAs are done
+  uint64_t* acc_full = empty + NS;                       // kAccBufs
   uint64_t* acc_empty = acc_full + kAccBufs;             // kAccBufs
   uint64_t* mma_done = acc_empty + kAccBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
@@ -435,8 +493,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   constexpr uint32_t kTmemCols = 128 * kAccBufs;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
-    for (int k = 0; k < G; ++k) mbar_init(&freed[k], 1);
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
     for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], kDrainWarps);
@@ -458,67 +518,95 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {                                     // ---- TMA producer ----
+      // load j = w S + i (window w, digit i, in the order the diagonals need them) goes to
+      // slot j mod NS once the slot's previous load, j - NS, has been consumed
       bool ok = true;
-      int wfull = 0, kpart = 0;                          // windows issued; groups of the next
+      int j = 0;                                         // loads issued
+      int q = 0, lap = 0;                                // j mod NS, j / NS (no divisions)
       for (int w = 0; w < nw && ok; ++w) {
         const int k0 = (w_begin + w) * OBK;
-        // digit groups in the order the previous window frees them: {0, S-1}, {1, S-2}, ...
-        // -- the low digits, which this window's first diagonals need, land first
-        for (int k = 0; k < G && ok; ++k) {
-          if (w > 0) ok = mbar_wait(&freed[k], (w - 1) & 1, a.status);
+        for (int i = 0; i < S; ++i, ++j) {
+          if (lap > 0) ok = mbar_wait(&empty[q], (lap - 1) & 1, a.status);
           if (!ok) break;
-          for (int i = k; ; i = S - 1 - k) {
-            mbar_expect_tx(&full[i], kDigitTileA + tile_b);
-            tma_load_2d(opA + i * kDigitTileA, &tmA, &full[i], k0, i * a.M + m0);
-            tma_load_2d(opB + i * tile_b, &tmB, &full[i], k0, i * a.BNt + n0);
-            if (i == S - 1 - k) break;
+          mbar_expect_tx(&full[q], kDigitTileA + tile_b);
+          if constexpr (MN) {
+            tma_load_2d(opA + q * kDigitTileA, &tmA, &full[q], m0, i * a.M + k0);
+            tma_load_2d(opA + q * kDigitTileA + kDigitTileA / 2, &tmA, &full[q], m0 + 64,
+                        i * a.M + k0);
+          } else {
+            tma_load_2d(opA + q * kDigitTileA, &tmA, &full[q], k0, i * a.M + m0);
           }
-          kpart = k + 1;
+          tma_load_2d(opB + q * tile_b, &tmB, &full[q], k0, i * a.BNt + n0);
+          if (++q == NS) {
+            q = 0;
+            ++lap;
+          }
         }
-        if (!ok) break;
-        wfull = w + 1;
-        kpart = 0;
-        if (w + 1 < nw) {                                // next window into L2 meanwhile
+        if (ok && w + 1 < nw) {                          // next window into L2 meanwhile
 #pragma unroll
           for (int i = 0; i < S; ++i) {
-            tma_prefetch_2d(&tmA, k0 + OBK, i * a.M + m0);
+            if constexpr (MN) {
+              tma_prefetch_2d(&tmA, m0, i * a.M + k0 + OBK);
+              tma_prefetch_2d(&tmA, m0 + 64, i * a.M + k0 + OBK);
+            } else {
+              tma_prefetch_2d(&tmA, k0 + OBK, i * a.M + m0);
+            }
             tma_prefetch_2d(&tmB, k0 + OBK, i * a.BNt + n0);
           }
         }
       }
-      for (int i = 0; i < S; ++i) {                      // copies must land before exit (the
-        const int grp = i < S - 1 - i ? i : S - 1 - i;   // earlier ones were consumed)
-        const int issued = wfull + (grp < kpart ? 1 : 0);
-        if (issued > 0) mbar_wait(&full[i], (issued - 1) & 1, a.status, false);
+      // copies must land before exit: the last load of each slot (earlier ones were consumed
+      // before the slot was refilled)
+      for (int q = 0; q < NS && q < j; ++q) {
+        const int loads = (j - 1 - q) / NS + 1;
+        mbar_wait(&full[q], (loads - 1) & 1, a.status, false);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {                                     // ---- MMA issuer ----
-      const uint32_t idesc = idesc_f16(OBM, BN);
-      uint64_t ad[S], bd[S];
-#pragma unroll
-      for (int i = 0; i < S; ++i) {
-        ad[i] = sw128_desc(su32(opA) + i * kDigitTileA);
-        bd[i] = sw128_desc(su32(opB) + i * tile_b);
-      }
+      const uint32_t idesc = idesc_f16(OBM, BN) | (MN ? (1u << 15) : 0u);
+      constexpr int kAStep = MN ? (16 * 128) >> 4 : 2;   // descriptor units per K = 16 step
+      // descriptors of slot 0; slot q lies q tiles further (start address in 16-byte units)
+      const uint64_t ad0 = MN ? sw128_desc_mn(su32(opA), kDigitTileA / 2) : sw128_desc(su32(opA));
+      const uint64_t bd0 = sw128_desc(su32(opB));
       bool ok = true;
       int g = 0;                                         // diagonals issued
+      int qb = 0, lb = 0;                                // slot and lap of load w S (digit 0)
       for (int w = 0; w < nw && ok; ++w) {
-        for (int d = 0; d < S && ok; ++d, ++g) {
+        uint64_t ad[S], bd[S];                           // this window's digits: slot (w S + i) mod NS
+        uint64_t* freed[S];
+        int qs[S], ph[S];                                // slot, and the parity of its load
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          const bool wrap = qb + i >= NS;                // S <= NS: at most one wrap
+          qs[i] = wrap ? qb + i - NS : qb + i;
+          ph[i] = (wrap ? lb + 1 : lb) & 1;
+          ad[i] = ad0 + static_cast<uint64_t>(qs[i] * (kDigitTileA >> 4));
+          bd[i] = bd0 + static_cast<uint64_t>(qs[i] * (tile_b >> 4));
+          freed[i] = &empty[qs[i]];
+        }
+        qb += S;
+        if (qb >= NS) {
+          qb -= NS;
+          ++lb;
+        }
+#pragma unroll
+        for (int d = 0; d < S; ++d, ++g) {
+          if (!ok) break;
           const int b = g % kAccBufs;
           if (g >= kAccBufs) ok = mbar_wait(&acc_empty[b], ((g / kAccBufs) - 1) & 1, a.status);
-          if (ok) ok = mbar_wait(&full[d], w & 1, a.status);
+          if (ok) ok = mbar_wait(&full[qs[d]], ph[d], a.status);
           if (!ok) break;
           tc_fence_after();
           const uint32_t acc = tmem + static_cast<uint32_t>(b * 128);
           switch (d) {
-            case 0: issue_diagonal<S, 0>(acc, ad, bd, idesc, freed); break;
-            case 1: issue_diagonal<S, 1>(acc, ad, bd, idesc, freed); break;
-            case 2: issue_diagonal<S, 2>(acc, ad, bd, idesc, freed); break;
-            case 3: issue_diagonal<S, 3>(acc, ad, bd, idesc, freed); break;
-            case 4: issue_diagonal<S, 4>(acc, ad, bd, idesc, freed); break;
-            case 5: issue_diagonal<S, 5>(acc, ad, bd, idesc, freed); break;
-            default: issue_diagonal<S, S - 1>(acc, ad, bd, idesc, freed); break;
+            case 0: issue_diagonal<S, 0, kAStep>(acc, ad, bd, idesc, freed); break;
+            case 1: issue_diagonal<S, 1, kAStep>(acc, ad, bd, idesc, freed); break;
+            case 2: issue_diagonal<S, 2, kAStep>(acc, ad, bd, idesc, freed); break;
+            case 3: issue_diagonal<S, 3, kAStep>(acc, ad, bd, idesc, freed); break;
+            case 4: issue_diagonal<S, 4, kAStep>(acc, ad, bd, idesc, freed); break;
+            case 5: issue_diagonal<S, 5, kAStep>(acc, ad, bd, idesc, freed); break;
+            default: issue_diagonal<S, S - 1, kAStep>(acc, ad, bd, idesc, freed); break;
           }
           mma_commit(&acc_full[b]);
         }
@@ -672,13 +760,23 @@ cudaError_t oz_scratch(size_t bytes, void** out) {
 
 size_t align1k(size_t b) { return (b + 1023) / 1024 * 1024; }
 
-size_t oz_smem_bytes(int S, int BN) {
-  return static_cast<size_t>(S) * (kDigitTileA + BN * 128) + 256 + 1024;   // tiles, barriers, align
+size_t oz_slot_bytes(int BN) { return static_cast<size_t>(kDigitTileA) + static_cast<size_t>(BN) * 128; }
+
+// Digit slots of the ring: as many as fit 227 KB (beyond S, the next window's first digits load
+// a window ahead), at least S.
+int oz_slots(int S, int BN) {
+  const size_t room = (kMaxNodeSmemBytes - 256 - 1024) / oz_slot_bytes(BN);
+  return std::max(S, std::min(kMaxSlots, static_cast<int>(room)));
+}
+
+size_t oz_smem_bytes(int S, int BN) {                   // tiles, barriers, alignment
+  return static_cast<size_t>(oz_slots(S, BN)) * oz_slot_bytes(BN) + 256 + 1024;
 }
 
 template <int S>
 cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const double* Om,
-                            const double* Ps, int s, double* Y, double* Z, cudaStream_t st) {
+                            const double* Ps, int s, double* Y, double* Z, bool shared,
+                            cudaStream_t st) {
   int BN, BNt;
   column_tiles(s, &BN, &BNt);
   const int64_t ldd = (N + 63) / 64 * 64;
@@ -695,7 +793,7 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
   const size_t b_planes = static_cast<size_t>(S) * BNt * ldd * 2;
   const size_t etab = static_cast<size_t>(N) * W * 2;
   const size_t off_yd = 1024, off_zd = off_yd + align1k(a_planes);
-  const size_t off_ey = off_zd + align1k(a_planes), off_ez = off_ey + align1k(etab);
+  const size_t off_ey = off_zd + (shared ? 0 : align1k(a_planes)), off_ez = off_ey + align1k(etab);
   const size_t off_bo = off_ez + align1k(etab), off_bp = off_bo + align1k(b_planes);
   const size_t off_eo = off_bp + align1k(b_planes), off_ep = off_eo + align1k(W * 2);
   const size_t off_rexp = off_ep + align1k(W * 2);
@@ -720,7 +818,10 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
   e = cudaMemsetAsync(status + kAbortWord, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
 
-  oz_split_a<S><<<dim3(W, W), 256, 0, st>>>(A, lda, N, Yd, Zd, ldd, EY, EZ, W, status);
+  if (shared)
+    oz_split_shared<S><<<dim3(W, W), 256, 0, st>>>(A, lda, N, Yd, ldd, EY, EZ, W, status);
+  else
+    oz_split_a<S><<<dim3(W, W), 256, 0, st>>>(A, lda, N, Yd, Zd, ldd, EY, EZ, W, status);
   oz_split_b<S><<<W, 256, 0, st>>>(Om, N, s, BNt, ldd, Bo, EO, status);
   oz_split_b<S><<<W, 256, 0, st>>>(Ps, N, s, BNt, ldd, Bp, EP, status);
   e = cudaGetLastError();
@@ -730,8 +831,10 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
   const uint64_t row_bytes = static_cast<uint64_t>(ldd) * 2;
   if (!make_map(&mAy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Yd, N, S * N, row_bytes, OBK, OBM,
                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B) ||
-      !make_map(&mAz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Zd, N, S * N, row_bytes, OBK, OBM,
-                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B) ||
+      !(shared ? make_map(&mAz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Yd, N, S * N, row_bytes, 64,
+                          OBK, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B)
+               : make_map(&mAz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Zd, N, S * N, row_bytes, OBK,
+                          OBM, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B)) ||
       !make_map(&mBo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bo, N, S * BNt, row_bytes, OBK, BN,
                 CU_TENSOR_MAP_SWIZZLE_128B) ||
       !make_map(&mBp, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bp, N, S * BNt, row_bytes, OBK, BN,
@@ -746,13 +849,22 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
   const dim3 grid(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits),
                   static_cast<unsigned>(BNt / BN));
   const unsigned rg = 152u * 8u;
-  OzArgs ay{static_cast<int>(N), W, BN, BNt, wchunk, EY, EO, partial, rexp, status};
+  const int slots = oz_slots(S, BN);
+  OzArgs ay{static_cast<int>(N), W, BN, BNt, wchunk, slots, EY, EO, partial, rexp, status};
   kernel<<<grid, kOzThreads, smem, st>>>(mAy, mBo, ay);
   oz_reduce<<<rg, 256, 0, st>>>(partial, rexp, splits, N, BNt, s, Y);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  OzArgs az{static_cast<int>(N), W, BN, BNt, wchunk, EZ, EP, partial, rexp, status};
-  kernel<<<grid, kOzThreads, smem, st>>>(mAz, mBp, az);
+  OzArgs az{static_cast<int>(N), W, BN, BNt, wchunk, slots, EZ, EP, partial, rexp, status};
+  if (shared) {
+    auto kernel_mn = oz_gemm<S, true>;
+    e = cudaFuncSetAttribute(kernel_mn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kernel_mn<<<grid, kOzThreads, smem, st>>>(mAz, mBp, az);
+  } else {
+    kernel<<<grid, kOzThreads, smem, st>>>(mAz, mBp, az);
+  }
   oz_reduce<<<rg, 256, 0, st>>>(partial, rexp, splits, N, BNt, s, Z);
   return cudaGetLastError();
 }
@@ -761,17 +873,17 @@ cudaError_t launch_products(const double* A, int64_t lda, int64_t N, const doubl
 
 cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, const double* Om,
                                    const double* Ps, int s, double* Y, double* Z, int digits,
-                                   cudaStream_t st) {
+                                   bool shared_planes, cudaStream_t st) {
   if (s < 1 || s > 256 || N < 1 || N > (int64_t(1) << 20) || lda < N)
     return cudaErrorInvalidValue;
   int BN, BNt;
   column_tiles(s, &BN, &BNt);
   if (oz_smem_bytes(digits, BN) > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
   switch (digits) {
-    case 4: return launch_products<4>(A, lda, N, Om, Ps, s, Y, Z, st);
-    case 5: return launch_products<5>(A, lda, N, Om, Ps, s, Y, Z, st);
-    case 6: return launch_products<6>(A, lda, N, Om, Ps, s, Y, Z, st);
-    case 7: return launch_products<7>(A, lda, N, Om, Ps, s, Y, Z, st);
+    case 4: return launch_products<4>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
+    case 5: return launch_products<5>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
+    case 6: return launch_products<6>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
+    case 7: return launch_products<7>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -33,6 +33,7 @@
 // a group holds columns q, q + 8, ... Reductions inside a group take 3 shuffles. The FP64 pipe
 // (2 DFMA per clock per SM on GB300) bounds the side kernel where a level has many nodes.
 #include <algorithm>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -293,9 +294,13 @@ __device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int
 
 // MINB: CTAs per SM the registers are budgeted for (3 or 4 where the test block is small enough
 // for that many tiles of shared memory per SM, so that more warps hide the FP64 latencies).
-template <int NS, int MINB>
+// PRE: the factorization of the test block was made beforehand by node_lq (its shared-memory
+// image in `lq`, lq_stride doubles per (node, side)) and is copied in instead of recomputed;
+// the same instructions made it, so the results are bit-identical.
+template <int NS, int MINB, bool PRE = false>
 __global__ void __launch_bounds__(THREADS, MINB)
-    node_side(const NodeTask* __restrict__ tasks, int row_splits, int* status) {
+    node_side(const NodeTask* __restrict__ tasks, int row_splits, int* status,
+              const double* __restrict__ lq = nullptr, int64_t lq_stride = 0) {
   extern __shared__ double smem[];
   const NodeTask tk = tasks[blockIdx.x];
   const int side = blockIdx.y;
@@ -308,16 +313,50 @@ __global__ void __launch_bounds__(THREADS, MINB)
   double* F = smem;                                    // n x ldF
   double* tau = F + static_cast<size_t>(n) * ldF;      // n
   double* rdiag = tau + n;                             // n
-  const double* T = side ? tk.Ps : tk.Om;
-  for (int e = threadIdx.x; e < n * s; e += THREADS) F[(e / s) * ldF + e % s] = T[e];
-  __syncthreads();
-  lq_factor<double>(F, ldF, n, s, tau, rdiag, status);
+  if constexpr (PRE) {
+    const double* img = lq + (2 * static_cast<int64_t>(blockIdx.x) + side) * lq_stride;
+    const int len = n * ldF + 2 * n;
+    for (int e = threadIdx.x; e < len; e += THREADS) F[e] = img[e];
+    __syncthreads();
+  } else {
+    const double* T = side ? tk.Ps : tk.Om;
+    for (int e = threadIdx.x; e < n * s; e += THREADS) F[(e / s) * ldF + e % s] = T[e];
+    __syncthreads();
+    lq_factor<double>(F, ldF, n, s, tau, rdiag, status);
+  }
   if (tk.is_root) {
     stream_rows<NS>(tk.Y, n, s, 0, row0, row1, F, ldF, tau, rdiag, nullptr, tk.D);
     return;
   }
   stream_rows<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, F, ldF, tau, rdiag,
                   side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
+}
+
+// The LQ of one test block alone (grid: node, side), its shared-memory image (F, tau, 1/beta:
+// side_smem_doubles(n, s) doubles) written to lq for node_side<.., PRE = true>. The test blocks
+// of the leaves need no sample, so this can run while the products are formed: registers are
+// budgeted at 40 per thread (six CTAs' worth per SM) so that a CTA fits beside a product
+// kernel's (e.g. 320 threads x 168 registers).
+__global__ void __launch_bounds__(THREADS, 6)
+    node_lq(const NodeTask* __restrict__ tasks, int* status, double* __restrict__ lq,
+            int64_t lq_stride) {
+  extern __shared__ double smem[];
+  const NodeTask tk = tasks[blockIdx.x];
+  const int side = blockIdx.y;
+  if (tk.is_root && side == 1) return;
+  const int n = tk.n, s = tk.s;
+  const int ldF = s + 1;
+  double* F = smem;
+  double* tau = F + static_cast<size_t>(n) * ldF;
+  double* rdiag = tau + n;
+  const double* T = side ? tk.Ps : tk.Om;
+  for (int e = threadIdx.x; e < n * s; e += THREADS) F[(e / s) * ldF + e % s] = T[e];
+  __syncthreads();
+  lq_factor<double>(F, ldF, n, s, tau, rdiag, status);
+  __syncthreads();
+  double* img = lq + (2 * static_cast<int64_t>(blockIdx.x) + side) * lq_stride;
+  const int len = n * ldF + 2 * n;
+  for (int e = threadIdx.x; e < len; e += THREADS) img[e] = F[e];
 }
 
 // ---- side kernel, cluster form: the C CTAs of a thread-block cluster share one LQ -----------
@@ -919,6 +958,10 @@ int side_row_splits(int ntasks, int n, int s) {
   return C >= 2 ? -C : 1;
 }
 
+int side_shape(int ntasks, int n, int s, int row_splits) {
+  return row_splits != 0 ? row_splits : side_row_splits(ntasks, n, s);
+}
+
 size_t side_cluster_smem_doubles(int n, int s, int C) {
   const size_t chunk = (static_cast<size_t>(n) + C - 1) / C;
   const size_t ld = static_cast<size_t>(cluster_ld(s));
@@ -931,12 +974,30 @@ bool side_cluster_fits(int n, int s, int C) {
          side_cluster_smem_doubles(n, s, C) * sizeof(double) <= kMaxNodeSmemBytes;
 }
 
+int64_t side_lq_stride(int max_n, int max_s) {
+  return static_cast<int64_t>(side_smem_doubles(max_n, max_s));
+}
+
+cudaError_t launch_side_lq(const NodeTask* d_tasks, int ntasks, int max_n, int max_s, double* lq,
+                           int* d_status, cudaStream_t st) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t bytes = side_smem_doubles(max_n, max_s) * sizeof(double);
+  if (max_s > kMaxS || bytes > kMaxNodeSmemBytes || lq == nullptr) return cudaErrorInvalidValue;
+  const dim3 grid(static_cast<unsigned>(ntasks), 2u);
+  cudaError_t e = allow_smem(node_lq);
+  if (e != cudaSuccess) return e;
+  node_lq<<<grid, THREADS, bytes, st>>>(d_tasks, d_status, lq, side_lq_stride(max_n, max_s));
+  return cudaGetLastError();
+}
+
 // The side kernel of one height. R > 0: R row slices per (node, side), each CTA factoring the
-// test block itself; R < 0: a cluster of -R CTAs per (node, side) sharing one factorization.
+// test block itself (or, with lq, copying the factorization node_lq left there); R < 0: a
+// cluster of -R CTAs per (node, side) sharing one factorization (lq must be NULL).
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
-                             int R, int* d_status, cudaStream_t st) {
+                             int R, int* d_status, cudaStream_t st, const double* lq) {
   if (ntasks <= 0) return cudaSuccess;
   if (max_s > kMaxS) return cudaErrorInvalidValue;
+  if (lq != nullptr && R < 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (R < 0) {
     const int C = std::min(-R, kMaxSideCluster);
@@ -970,31 +1031,38 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
   // CTA) fit; the register budget follows (64, 80 or 128 per thread, no spills)
   const int fit = static_cast<int>((228 * 1024) / (side_bytes + 1024));
   const dim3 grid(static_cast<unsigned>(ntasks), 2u, static_cast<unsigned>(splits));
+  const int64_t stride = side_lq_stride(max_n, max_s);
   auto side = [&](auto kernel) {
     e = allow_smem(kernel);
     if (e == cudaSuccess) {
-      kernel<<<grid, THREADS, side_bytes, st>>>(d_tasks, splits, d_status);
+      kernel<<<grid, THREADS, side_bytes, st>>>(d_tasks, splits, d_status, lq, stride);
       e = cudaGetLastError();
     }
   };
-  if (max_s <= 8 * G) {
-    if (fit >= 4) side(node_side<8, 4>);
-    else if (fit == 3) side(node_side<8, 3>);
-    else side(node_side<8, 2>);
-  } else if (max_s <= 16 * G) {
-    if (fit >= 4) side(node_side<16, 4>);
-    else if (fit == 3) side(node_side<16, 3>);
-    else side(node_side<16, 2>);
-  } else {
-    if (fit >= 3) side(node_side<24, 3>);
-    else side(node_side<24, 2>);
-  }
+  auto pick = [&](auto pre) {
+    constexpr bool P = decltype(pre)::value;
+    if (max_s <= 8 * G) {
+      if (fit >= 4) side(node_side<8, 4, P>);
+      else if (fit == 3) side(node_side<8, 3, P>);
+      else side(node_side<8, 2, P>);
+    } else if (max_s <= 16 * G) {
+      if (fit >= 4) side(node_side<16, 4, P>);
+      else if (fit == 3) side(node_side<16, 3, P>);
+      else side(node_side<16, 2, P>);
+    } else {
+      if (fit >= 3) side(node_side<24, 3, P>);
+      else side(node_side<24, 2, P>);
+    }
+  };
+  if (lq != nullptr) pick(std::true_type{});
+  else pick(std::false_type{});
   return e;
 }
 
 cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, int max_r,
                                int max_s, int finish, int row_splits, int* d_status,
-                               cudaStream_t st, cudaEvent_t* marks, FinishShape shape) {
+                               cudaStream_t st, cudaEvent_t* marks, FinishShape shape,
+                               const double* lq) {
   if (ntasks <= 0) return cudaSuccess;
   auto mark = [&](int i) { return marks ? cudaEventRecord(marks[i], st) : cudaSuccess; };
   if (max_s > kMaxS) return cudaErrorInvalidValue;
@@ -1019,9 +1087,8 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
     return cudaErrorInvalidValue;
   cudaError_t e = mark(0);
   if (e == cudaSuccess)
-    e = launch_side_only(d_tasks, ntasks, max_n, max_s,
-                         row_splits != 0 ? row_splits : side_row_splits(ntasks, max_n, max_s),
-                         d_status, st);
+    e = launch_side_only(d_tasks, ntasks, max_n, max_s, side_shape(ntasks, max_n, max_s, row_splits),
+                         d_status, st, lq);
   if (e == cudaSuccess) e = mark(1);
   if (e != cudaSuccess) return e;
   // bases: one CTA per (node, side); the register slots span the n <= s columns of a basis

@@ -116,6 +116,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          (static_cast<uint64_t>(2) << 61);
 }
 
+// Shared-memory matrix descriptor of an MN-major operand with 128-byte swizzle: rows of 64
+// 16-bit elements along M (or N), 8-row groups 1024 B apart along K (stride byte offset), the
+// next 64-element atom along M `atom_bytes` further (leading byte offset).
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t atom_bytes) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) |
+         (static_cast<uint64_t>((atom_bytes >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>(1024 >> 4) << 32) | (static_cast<uint64_t>(1) << 46) |
+         (static_cast<uint64_t>(2) << 61);
+}
+
 // Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 accumulator, M x N.
 // Instruction descriptor of tcgen05.mma kind::f16 with FP16 A and B (F32 accumulator).
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {

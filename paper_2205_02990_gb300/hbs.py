@@ -37,7 +37,8 @@ EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan"
             "hbs_tree_build", "hbs_get_node", "hbs_factor_bytes", "hbs_copy_factors",
             "hbs_apply_static", "hbs_sample_sync", "hbs_apply_batch", "hbs_load_factors",
             "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph",
-            "hbs_test_inject_status", "hbs_probe_peaks", "hbs_profile_sweep", "hbs_probe_dmma"]
+            "hbs_test_inject_status", "hbs_probe_peaks", "hbs_profile_sweep", "hbs_probe_dmma",
+            "hbs_sample_execute"]
 
 
 class HBSError(RuntimeError):
@@ -89,6 +90,8 @@ def load():
         "hbs_set_graph": (c.c_int, [c.c_void_p, c.c_int]),
         "hbs_plan": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p)]),
         "hbs_execute": (c.c_int, [c.c_void_p, c.POINTER(_Problem), c.c_void_p]),
+        "hbs_sample_execute": (c.c_int, [c.c_void_p, c.POINTER(_Operator), c.c_uint64, c.c_int32,
+                                         c.POINTER(_Problem), c.c_void_p]),
         "hbs_compress": (c.c_int, [c.c_int32, c.POINTER(_Problem), c.c_int32, c.POINTER(c.c_void_p),
                                    c.c_void_p]),
         "hbs_apply": (c.c_int, [c.c_void_p, c.c_int32, c.c_int, c.c_int32, c.c_void_p, c.c_void_p,
@@ -270,6 +273,17 @@ def hbs_execute(handle, problems=None):
     problems = handle.problems if problems is None else list(problems)
     _check(load().hbs_execute(handle.ptr, _problems(problems), _stream()))
     handle.problems = problems
+
+
+def hbs_sample_execute(handle, A, seed, precision=HBS_PREC_FP64, problems=None, N=None):
+    """hbs_sample into the problem's Omega, Psi, Y, Z, then hbs_execute, with the leaves'
+    test-block LQ on a second stream while the products run (a one-problem handle)."""
+    problems = handle.problems if problems is None else list(problems)
+    op, keep, _ = _operator(A, problems[0].N if N is None else N)
+    _check(load().hbs_sample_execute(handle.ptr, ctypes.byref(op), seed, precision,
+                                     _problems(problems), _stream()))
+    handle.problems = problems
+    del keep
 
 
 def hbs_compress(problems, precision=HBS_PREC_FP64):

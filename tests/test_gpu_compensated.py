@@ -1,7 +1,8 @@
 """The compensated mixed precision (HBS_PREC_MIXED_COMPENSATED) against the FP64 oracle.
 
 Products: the FP64 A and test matrices written as 5 exact 8-bit digits per entry (one exponent
-per 64-wide block), the 15 digit pairs with i + j <= 4 multiplied on the tensor cores with
+per 64 x 64 block of A, read transposed for A^*, and per 64-row window of a test matrix), the
+15 digit pairs with i + j <= 4 multiplied on the tensor cores with
 exactly representable FP32 sums. Each entry is represented to 2^-39 of its block's largest
 magnitude and each dropped pair weighs at most 6 * 2^-38 of the product of the block maxima, so
 an output entry errs by ~2^-36 times sum_k (max|a| max|b|) over its windows; for these inputs the
@@ -75,6 +76,28 @@ def test_compensated_products(hb, N, s, kind):
     assert rel(host(Y), Yr) <= 1e-10 and rel(host(Z), Zr) <= 1e-10
     assert np.max(np.abs(host(Y) - Yr) / (np.abs(A) @ np.abs(Om))) <= 1e-9
     assert np.max(np.abs(host(Z) - Zr) / (np.abs(A).T @ np.abs(Ps))) <= 1e-9
+
+
+def test_compensated_products_graded_rows_and_columns(hb):
+    """Rows and columns of A graded over 2^-20 .. 2^20: one exponent per 64 x 64 block keeps
+    the normwise bound (a numpy model of the rounding to 2^-39 of each block's largest entry
+    gives 2.1e-11), while entries far below their block's largest lose relative accuracy (the
+    same model: 0.44 of sum_k |a_k b_k| at worst). HBS_PREC_FP64_TC, one exponent per row (per
+    column for A^*) and window, keeps the per-entry bound on the same matrix."""
+    N, s = 1000, 64
+    rng = np.random.default_rng(7)
+    dr, dc = 2.0 ** rng.integers(-20, 21, N), 2.0 ** rng.integers(-20, 21, N)
+    A = dr[:, None] * gaussian((N, N), 11) * dc[None, :]
+    Om, Ps = gaussian((N, s), 1), gaussian((N, s), 2)
+    Yr, Zr = A @ Om, A.T @ Ps
+    for precision in (CMP, 3):
+        Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(2))
+        hb.hbs_sample_products(dev(A), s, dev(Om), dev(Ps), Y, Z, precision=precision)
+        hb.hbs_sample_sync()
+        assert rel(host(Y), Yr) <= 1e-10 and rel(host(Z), Zr) <= 1e-10
+        if precision == 3:
+            assert np.max(np.abs(host(Y) - Yr) / (np.abs(A) @ np.abs(Om))) <= 1e-12
+            assert np.max(np.abs(host(Z) - Zr) / (np.abs(A).T @ np.abs(Ps))) <= 1e-12
 
 
 def _worst_factor(hb, h, F, blk, L, item=0):

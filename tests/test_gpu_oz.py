@@ -78,10 +78,15 @@ def exact_dot(a, b):
     return math.fsum(np.concatenate([p, e]))
 
 
-def sample_tc(hb, A, s, seed):
+CMP = 4   # HBS_PREC_MIXED_COMPENSATED: 5 digits, one exponent per 64 x 64 block of A
+# relative Frobenius bound of the scaled products per precision (5 digits: ~2^-36 per entry)
+SCALED_BOUND = {TC: 1e-13, CMP: 1e-10}
+
+
+def sample_tc(hb, A, s, seed, precision=TC):
     N = A.shape[0]
     Om, Ps, Y, Z = (torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4))
-    hb.hbs_sample(dev(A), s, seed, Om, Ps, Y, Z, precision=TC)
+    hb.hbs_sample(dev(A), s, seed, Om, Ps, Y, Z, precision=precision)
     hb.hbs_sample_sync()
     return [host(x) for x in (Om, Ps, Y, Z)]
 
@@ -133,35 +138,38 @@ def test_rows_and_columns_over_a_wide_range(hb):
     check_entries(A, Om, Y, [0, 17, 130, 1499], [0, 39])
 
 
-def test_scale_far_from_one(hb):
+@pytest.mark.parametrize("precision", [TC, CMP])
+def test_scale_far_from_one(hb, precision):
     # the whole FP64 exponent range: A ~ 2^-600 and A ~ 2^+600 give the scaled products
     N, s = 300, 20
     G = gaussian((N, N), 4)
     for e in (-600, 600):
         A = np.ldexp(G, e)
-        Om, Ps, Y, Z = sample_tc(hb, A, s, 9)
-        assert rel(np.ldexp(Y, -e), G @ Om) <= 1e-13
-        assert rel(np.ldexp(Z, -e), G.T @ Ps) <= 1e-13
+        Om, Ps, Y, Z = sample_tc(hb, A, s, 9, precision)
+        assert rel(np.ldexp(Y, -e), G @ Om) <= SCALED_BOUND[precision]
+        assert rel(np.ldexp(Z, -e), G.T @ Ps) <= SCALED_BOUND[precision]
 
 
-def test_subnormal_operator(hb):
+@pytest.mark.parametrize("precision", [TC, CMP])
+def test_subnormal_operator(hb, precision):
     # A ~ 2^-1040: every entry subnormal (~34 significant bits). Its digits need left shifts of
     # the mantissa by up to ~21 bits; the products land on the subnormal grid (2^-1074), so they
     # match the exact product to its rounding, 2^-1074 per entry (~1e-10 relative here).
     N, s = 300, 20
     A = np.ldexp(gaussian((N, N), 6), -1040)
     Gs = np.ldexp(A, 1040)                             # exactly A's values, scaled up
-    Om, Ps, Y, Z = sample_tc(hb, A, s, 10)
+    Om, Ps, Y, Z = sample_tc(hb, A, s, 10, precision)
     assert rel(np.ldexp(Y, 1040), Gs @ Om) <= 1e-8
     assert rel(np.ldexp(Z, 1040), Gs.T @ Ps) <= 1e-8
 
 
-def test_non_finite_entry_is_reported(hb):
+@pytest.mark.parametrize("precision", [TC, CMP])
+def test_non_finite_entry_is_reported(hb, precision):
     N, s = 200, 12
     A = gaussian((N, N), 2)
     A[3, 150] = np.nan
     X = [torch.empty((N, s), dtype=torch.float64, device="cuda") for _ in range(4)]
-    hb.hbs_sample(dev(A), s, 1, *X, precision=TC)
+    hb.hbs_sample(dev(A), s, 1, *X, precision=precision)
     with pytest.raises(hb.HBSError) as e:
         hb.hbs_sample_sync()
     assert e.value.code == -5
@@ -179,11 +187,12 @@ def test_digit_products_need_a_dense_fp64_operator(hb):
     assert e.value.code == -8
 
 
-def test_repeated_calls_are_bit_identical(hb):
+@pytest.mark.parametrize("precision", [TC, CMP])
+def test_repeated_calls_are_bit_identical(hb, precision):
     N, s = 1000, 30
     A = log_kernel(N)
-    first = sample_tc(hb, A, s, 4)
-    second = sample_tc(hb, A, s, 4)
+    first = sample_tc(hb, A, s, 4, precision)
+    second = sample_tc(hb, A, s, 4, precision)
     for a, b in zip(first, second):
         assert np.array_equal(a, b)
 
