@@ -780,10 +780,18 @@ def main():
         hb.hbs_sample_products(Aop, s, Om, Ps, Y, Z, precision=cfg["sample"])
         hb.hbs_execute(h, [prob])
         hb.hbs_autotune(h)                                 # side shape per height (plan time)
+        plain_steps = min(steps, 5)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
+              for _ in range(plain_steps)]
 
-        def step(i=None, A_src=None):
+        def step(A_src=None):
+            # the library's one call: draws, products, sweep, with the leaves' test-block LQ on
+            # a second stream while the products run
+            hb.hbs_sample_execute(h, Aop if A_src is None else A_src, seed,
+                                  precision=cfg["sample"], problems=[prob])
+
+        def plain_step(i=None, A_src=None):
+            # the same work as separate calls, nothing overlapped; the products between events
             hb.hbs_draw_gaussian(N, s, 0, seed, Om)
             hb.hbs_draw_gaussian(N, s, 1, seed, Ps)
             if i is not None:
@@ -794,34 +802,40 @@ def main():
                 ev[i][1].record(stream)
             hb.hbs_execute(h, [prob])
 
+        def run_timed(fn, k):
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(k):
+                fn(i)
+            b.record(stream)
+            barrier()
+            return max_over_ranks(a.elapsed_time(b) / 1e3)
+
         for _ in range(warmup):
             step()
         hb.hbs_sync_status(h)
         hb.hbs_sample_sync()
-        barrier()
-        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         clk = ClockSampler(gpu_id) if sample_clocks else None
         if clk:
             clk.__enter__()
-        barrier()
-        start.record(stream)
-        for i in range(steps):
-            step(i)
-        stop.record(stream)
-        barrier()
+        elapsed = run_timed(lambda i: step(), steps)
         if clk:
             clk.__exit__(None, None, None)
+        plain_step()
+        elapsed_plain = run_timed(plain_step, plain_steps)
         hb.hbs_sync_status(h)
         hb.hbs_sample_sync()
-        elapsed = max_over_ranks(start.elapsed_time(stop) / 1e3)
-        per_launch = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * steps)
+        per_launch = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (2 * plain_steps)
         phases = hb.hbs_profile_sweep(h)                   # one more sweep, events per launch
 
         def products_ms():                                 # of the steps timed with events
-            return sum(a.elapsed_time(b) for a, b in ev) / steps
+            return sum(a.elapsed_time(b) for a, b in ev) / plain_steps
 
-        return dict(h=h, step=step, elapsed=elapsed, per_launch=per_launch, products_ms=products_ms,
-                    clocks=clk.summary() if clk else None, tuning=hb.hbs_get_tuning(h),
+        return dict(h=h, step=step, plain_step=plain_step, plain_steps=plain_steps,
+                    elapsed=elapsed, elapsed_plain=elapsed_plain, per_launch=per_launch,
+                    products_ms=products_ms, clocks=clk.summary() if clk else None,
+                    tuning=hb.hbs_get_tuning(h),
                     sweep=sweep_roofline(phases, N, r, s, leaf, FINISH[cfg["sweep"]], peaks))
 
     def power_norm(apply_B, apply_Bt, steps=20):
@@ -872,12 +886,12 @@ def main():
         dst = src                                   # the device copy the step multiplies
         streamed = cfg["sample"] == 0               # FP64 products take the pinned A directly
 
-        def e2e_step(k=None):
+        def e2e_step(k=None, step=res["step"]):
             if streamed:                            # row blocks copied under the products
-                res["step"](k, A_src=A_host)
+                step(A_src=A_host)
             else:
                 dst.copy_(A_host, non_blocking=True)
-                res["step"](k)
+                step()
             hb.hbs_copy_factors(h, F_host)
 
         e2e_step()
@@ -898,6 +912,10 @@ def main():
         c[2].record(stream)
         barrier()
         h2d_ms, d2h_ms = c[0].elapsed_time(c[1]), c[1].elapsed_time(c[2])
+        # the products of the same steps alone, between events (the plain calls)
+        for k in range(res["plain_steps"]):
+            e2e_step(step=lambda A_src=None, k=k: res["plain_step"](k, A_src=A_src))
+        torch.cuda.synchronize()
         streamed_products_ms = res["products_ms"]()          # both products, per e2e step
         a_bytes = src.numel() * src.element_size()
         e2e_ms = te / args.steps * 1e3
@@ -966,15 +984,24 @@ def main():
         # splits + 2 GEMMs + 2 reductions; digits: 2 test-matrix splits + 1 A split + 2 GEMMs +
         # 2 reductions), then per tree level the side, bases, D and merge kernels (FP64: D in two
         # kernels; FP32: one)
+        # (+ node_lq, the leaves' LQ, where the leaf height runs the one-CTA side form)
         "gpu_launches": args.steps * ({0: 2 + 2 + 2, 1: 2 + 6, 2: 2 + 6, 3: 2 + 3 + 4,
                                        4: 2 + 3 + 4}[MODES[head]["sample"]]
+                                      + (1 if res["tuning"][0] > 0 else 0)
                                       + sweep_launches(N, r, s, leaf, res["tuning"],
                                                        MODES[head]["sweep"] in (1, 2, 4))),
         "roofline": dict(roofline, sweep=res["sweep"]),
         "peaks": peaks,
         "clocks": res["clocks"],
+        "step": "hbs_sample_execute: Philox draws, products and sweep in one call, the leaves' "
+                "test-block LQ on a second stream while the products run (Section 1's single-view "
+                "remark); plain_ms_per_step: hbs_draw_gaussian x2 + hbs_sample_products + "
+                "hbs_execute, nothing overlapped",
         "modes": {m: {"ms_per_step": rr["elapsed"] / args.steps * 1e3,
                       "value": world * N * s * args.steps / rr["elapsed"],
+                      "plain_ms_per_step": rr["elapsed_plain"] / rr["plain_steps"] * 1e3,
+                      "overlap_saving_ms_per_step": (rr["elapsed_plain"] / rr["plain_steps"]
+                                                     - rr["elapsed"] / args.steps) * 1e3,
                       "rel_error": rr.get("rel_error"), "vs_fp64": rr.get("vs_fp64"),
                       "products_ms_per_launch": rr["per_launch"] * 1e3,
                       "sweep_ms": rr["sweep"]["total"]["ms"],
