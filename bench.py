@@ -383,7 +383,10 @@ def peaks_now(hb):
     fp32 = SM_COUNT_GB300 * 128 * 2 * 2070e6 / 1e12
     return {"fp64_derived": FP64_TFLOPS, "fp32_derived": fp32,
             "df32_derived": fp32 / DF32_SLOTS, "fp64_probe": fp64_probe, "fp32_probe": fp32_probe,
-            "df32_from_probe": fp32_probe / DF32_SLOTS, "fp64_dmma_probe": hb.hbs_probe_dmma()}
+            "df32_from_probe": fp32_probe / DF32_SLOTS, "fp64_dmma_probe": hb.hbs_probe_dmma(),
+            # cycles per M = N = 128, K = 16 tcgen05 MMA issued by one thread, alone and beside
+            # FP32 work (the bound of the drain-heavy digit GEMM)
+            "mma_issue_cycles": hb.hbs_probe_mma_issue()}
 
 
 def sweep_roofline(phase_ms, N, r, s, leaf, finish, peaks):

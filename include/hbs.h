@@ -338,6 +338,17 @@ int hbs_probe_peaks(double* fp64_tflops, double* fp32_tflops, void* cuda_stream)
  * Synchronizes cuda_stream; allocates 16 bytes. Errors: HBS_ERR_ARG, HBS_ERR_NOMEM, HBS_ERR_CUDA. */
 int hbs_probe_dmma(double* tflops, void* cuda_stream);
 
+/* No counterpart in the paper: a probe of the tcgen05 MMA issue rate behind the digit products'
+ * bound. On every SM one thread issues back-to-back M = N = 128, K = 16 FP16 MMAs while eight
+ * other warps of the CTA are idle (cycles_per_mma[0]), run FP32 TwoSum chains (cycles_per_mma[1])
+ * or run them only on the three warp schedulers the issuing warp does not use
+ * (cycles_per_mma[2]); each entry is SM clock cycles per MMA, averaged over the SMs. The tensor
+ * pipe's own rate is 64 cycles per MMA on GB300. Synchronizes the stream; allocates and frees a
+ * few bytes of device memory.
+ * Errors: HBS_ERR_ARG (NULL), HBS_ERR_TIMEOUT (the bounded wait for the MMAs gave up),
+ * HBS_ERR_CUDA. */
+int hbs_probe_mma_issue(double* cycles_per_mma, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------------------
  * Apply without allocating (no counterpart in the paper; a service of this library).
  *

@@ -4,8 +4,11 @@
 // kernels. Not part of the method; exported for the benchmark (hbs_probe_peaks in hbs.h).
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/hbs.h"
 #include "hbs_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace hbs {
 namespace {
@@ -96,8 +99,135 @@ cudaError_t time_dmma(int blocks, int iters, double* sink, cudaStream_t st, doub
   return e;
 }
 
+// tcgen05 MMA issue rate: one thread of warp 1 issues back-to-back M = N = 128, K = 16 MMAs
+// (kind::f16, zeroed FP16 operands in shared memory, four accumulators in tensor memory); the
+// other eight warps (4 .. 11) do nothing (mode 0), run FP32 TwoSum chains (mode 1), or run them
+// only where they do not share warp 1's scheduler, warp % 4 != 1 (mode 2). One CTA per SM.
+// cycles[blockIdx.x] = clock cycles from the first issue to the completion of the last MMA.
+constexpr int kMmaProbeThreads = 384;
+constexpr int kMmaProbeSmem = 200 * 1024;      // one CTA per SM
+
+__global__ void __launch_bounds__(kMmaProbeThreads, 1)
+    mma_issue_probe(int iters, int mode, unsigned long long* cycles, float* sink, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
+  uint8_t* A = smem;                       // 128 x 64 FP16, 128-byte swizzle
+  uint8_t* B = smem + 16384;               // 128 x 64 FP16
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int done;
+  const int warp = threadIdx.x / 32;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    done = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < 32768 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(smem)[i] = 0u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(&tslot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  if (threadIdx.x == 32) {
+    const uint64_t ad = sw128_desc(su32(A)), bd = sw128_desc(su32(B));
+    const uint32_t idesc = idesc_f16(128, 128);
+    const unsigned long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t acc = tmem + static_cast<uint32_t>((i & 3) * 128);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc),
+            "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(kk)
+            : "memory");
+      }
+    }
+    mma_commit(&bar);
+    mbar_wait(&bar, 0, status, false);
+    cycles[blockIdx.x] = clock64() - t0;
+    done = 1;
+  } else if (warp >= 4 && (mode == 1 || (mode == 2 && (warp & 3) != 1))) {
+    float hi[16], lo[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      hi[j] = 1e-3f * threadIdx.x + j;
+      lo[j] = 0.f;
+    }
+    while (!done) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {              // TwoSum of hi[j] and a neighbour's multiple
+        const float v = __fmul_rn(hi[(j + 1) & 15], 1.0001f);
+        const float t = __fadd_rn(hi[j], v);
+        const float bp = __fsub_rn(t, hi[j]);
+        lo[j] = __fadd_rn(lo[j], __fadd_rn(__fsub_rn(hi[j], __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+        hi[j] = __fmul_rn(t, 0.5f);
+      }
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc += hi[j] + lo[j];
+    if (acc == -1.f) *sink = acc;                  // never true: keeps the chains alive
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
 }  // namespace
 }  // namespace hbs
+
+extern "C" int hbs_probe_mma_issue(double* cycles_per_mma, void* cuda_stream) {
+  if (!cycles_per_mma) return HBS_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return HBS_ERR_CUDA;
+  unsigned long long* cyc = nullptr;
+  int* status = nullptr;
+  float* sink = nullptr;
+  e = cudaMalloc(&cyc, sizeof(unsigned long long) * sms);
+  if (e == cudaSuccess) e = cudaMalloc(&status, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(hbs::mma_issue_probe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             hbs::kMmaProbeSmem);
+  constexpr int kIters = 2000;                     // 8000 MMAs per CTA
+  std::vector<unsigned long long> h(sms);
+  for (int mode = 0; mode < 3 && e == cudaSuccess; ++mode) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first launch warms up
+      hbs::mma_issue_probe<<<sms, hbs::kMmaProbeThreads, hbs::kMmaProbeSmem, st>>>(
+          kIters, mode, cyc, sink, status);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h.data(), cyc, sizeof(unsigned long long) * sms, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    double mean = 0.0;
+    for (int b = 0; b < sms; ++b) mean += static_cast<double>(h[b]);
+    cycles_per_mma[mode] = e == cudaSuccess ? mean / sms / (4.0 * kIters) : 0.0;
+  }
+  int stat = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&stat, status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(cyc);
+  cudaFree(status);
+  cudaFree(sink);
+  if (e != cudaSuccess) return HBS_ERR_CUDA;
+  return (stat & hbs::kStatusTimeout) ? HBS_ERR_TIMEOUT : HBS_OK;
+}
 
 extern "C" int hbs_probe_dmma(double* tflops, void* cuda_stream) {
   if (!tflops) return HBS_ERR_ARG;

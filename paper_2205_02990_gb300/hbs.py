@@ -38,7 +38,7 @@ EXPORTED = ["hbs_draw_gaussian", "hbs_sample", "hbs_sample_products", "hbs_plan"
             "hbs_apply_static", "hbs_sample_sync", "hbs_apply_batch", "hbs_load_factors",
             "hbs_autotune", "hbs_get_tuning", "hbs_set_tuning", "hbs_set_graph",
             "hbs_test_inject_status", "hbs_probe_peaks", "hbs_profile_sweep", "hbs_probe_dmma",
-            "hbs_sample_execute"]
+            "hbs_sample_execute", "hbs_probe_mma_issue"]
 
 
 class HBSError(RuntimeError):
@@ -100,6 +100,7 @@ def load():
         "hbs_test_inject_status": (c.c_int, [c.c_void_p, c.c_int32]),
         "hbs_probe_peaks": (c.c_int, [c.POINTER(c.c_double), c.POINTER(c.c_double), c.c_void_p]),
         "hbs_probe_dmma": (c.c_int, [c.POINTER(c.c_double), c.c_void_p]),
+        "hbs_probe_mma_issue": (c.c_int, [c.POINTER(c.c_double), c.c_void_p]),
         "hbs_profile_sweep": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int32,
                                         c.POINTER(c.c_int32)]),
         "hbs_free": (None, [c.c_void_p]),
@@ -409,6 +410,15 @@ def hbs_probe_dmma():
     a = ctypes.c_double()
     _check(load().hbs_probe_dmma(ctypes.byref(a), _stream()))
     return a.value
+
+
+def hbs_probe_mma_issue():
+    """Cycles per tcgen05 MMA (M = N = 128, K = 16) issued by one thread: with the CTA's other
+    warps idle, with FP32 work on every warp scheduler, and with FP32 work only on the schedulers
+    the issuing warp does not use (measured now, one CTA per SM)."""
+    a = (ctypes.c_double * 3)()
+    _check(load().hbs_probe_mma_issue(a, _stream()))
+    return {"alone": a[0], "fp32_all_schedulers": a[1], "fp32_other_schedulers": a[2]}
 
 
 def hbs_free(handle):
