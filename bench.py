@@ -496,7 +496,10 @@ def run_batched(hb, torch, items=256, seed=SEED + 400, reps=3):
         out[name] = {"T2_sweep_ms": t2, "T1_total_ms": t1, "value_T2": total_ns / (t2 / 1e3),
                      "value_T1": total_ns / (t1 / 1e3), "rel_error_probe_max": max(errs),
                      "rel_error_probe_median": float(np.median(errs)),
-                     "tuned_row_slices": hb.hbs_get_tuning(h)}
+                     "tuned_row_slices": hb.hbs_get_tuning(h),
+                     # every tree of the batch in each launch; the sweep replayed from one graph
+                     "launches_per_height": "side 1, bases 1, D " + ("2 (FP64)" if name == "fp64" else "1")
+                                            + ", merges 1"}
         h.free()
     gen.free()
     return out
