@@ -24,7 +24,7 @@
 namespace hbs {
 namespace {
 
-constexpr int BM = 64, BN = 128, BK = 16, THREADS = 256;   // BN: widest column tile
+constexpr int BM = 64, BK = 16, THREADS = 256;   // rows of a tile, reduction step, threads
 constexpr int ASTRIDE = BM + 1;   // padded so that the transposing stores of op(A) = A hit
                                   // distinct banks
 
