@@ -98,6 +98,8 @@ def test_null_arguments_rejected(lib):
     assert lib.hbs_sync_status(None, None) == -1
     lib.hbs_free(None)                                   # NULL-safe
     assert lib.hbs_tree_build(0, 4, ctypes.byref(ctypes.c_int32()), None, None, 0) == -1
+    assert lib.hbs_sample_execute(None, None, 1, 0, None, None) == -1
+    assert lib.hbs_probe_mma_issue(None, None) == -1
 
 
 def test_unsupported_precision(lib):
