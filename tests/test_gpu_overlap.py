@@ -122,6 +122,20 @@ def test_black_box_operator_exact_hbs_recovery(hb):
     h1.free()
 
 
+def test_pinned_host_operator_is_bit_identical(hb):
+    # A in page-locked host memory: the FP64 products stream it through the device in row
+    # blocks on the caller's stream while the leaves' LQ runs on the handle's stream
+    N, r, s, leaf = 4096, 20, 60, 32
+    A = torch.as_tensor(log_kernel(N)).pin_memory()
+    h0, x0 = plain(hb, A, N, r, s, leaf, 13, FP64, FP64)
+    h1, x1 = overlapped(hb, A, N, r, s, leaf, 13, FP64, FP64, calls=2)
+    for a, b in zip(x0, x1):
+        assert torch.equal(a, b)
+    assert torch.equal(factors(hb, h0), factors(hb, h1))
+    h0.free()
+    h1.free()
+
+
 def test_sample_execute_argument_errors(hb):
     N, r, s, leaf = 512, 8, 30, 16
     x = blocks(N, s)
