@@ -28,27 +28,31 @@ constexpr int BM = 64, BK = 16, THREADS = 256;   // rows of a tile, reduction st
 constexpr int ASTRIDE = BM + 1;   // padded so that the transposing stores of op(A) = A hit
                                   // distinct banks
 
-// TJ = columns per thread: the CTA's column tile is 16 TJ wide (TJ = 8 for s > 112, fewer for
-// narrower s, so that s = 90 or s = 30 does not pad to 128 columns).
+// TJ = column slots per thread: the CTA's column tile is 8 TJ wide (TJ = ceil(s/8) <= 16, wider s
+// in tiles of 128), 8 column lanes x 32 row pairs per CTA. A warp covers 8 columns of each slot,
+// so a slot lies wholly inside or wholly past s: s = 120 computes 120 columns, not 128. (Each
+// FP64 warp instruction occupies its scheduler's FP64 unit for the same time however many of its
+// lanes do useful work, so a half-used slot would cost a whole one.)
 template <bool TRANS, int TJ>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2)
     sample_gemm_f64(const double* __restrict__ A, int64_t lda, int64_t M, int64_t K,
                     const double* __restrict__ B, int s, double* __restrict__ C, int64_t kslice,
                     int64_t ldc_split) {
-  constexpr int TBN = 16 * TJ;
+  constexpr int TBN = 8 * TJ;
+  constexpr int kBLoads = (BK * TBN + THREADS - 1) / THREADS;
   __shared__ double As[BK][ASTRIDE];   // As[k][m] = op(A)[m0 + m][k0 + k]
   __shared__ double Bs[BK][TBN];       // Bs[k][c] = B[k0 + k][c0 + c]
   const int tid = threadIdx.x;
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % 8, ty = tid / 8;                     // column lane, row pair
   const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
   const int c0 = blockIdx.y * TBN;
   const int64_t kbeg = static_cast<int64_t>(blockIdx.z) * kslice;
   const int64_t kend = min(K, kbeg + kslice);
   C += static_cast<int64_t>(blockIdx.z) * ldc_split;        // this slice's partial (or C itself)
 
-  double acc[4][TJ];
+  double acc[2][TJ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < TJ; ++j) acc[i][j] = 0.0;
 
@@ -67,37 +71,39 @@ __global__ void __launch_bounds__(THREADS)
         As[k][m] = (gm < M && gk < kend) ? A[gk * lda + gm] : 0.0;
       }
     }
-    // B tile: BK x TBN doubles, TJ per thread
+    // B tile: BK x TBN doubles
 #pragma unroll
-    for (int e = 0; e < TJ; ++e) {
+    for (int e = 0; e < kBLoads; ++e) {
       const int idx = tid + e * THREADS;
-      const int c = idx % TBN, k = idx / TBN;
-      const int64_t gk = k0 + k;
-      const int gc = c0 + c;
-      Bs[k][c] = (gk < kend && gc < s) ? B[gk * s + gc] : 0.0;
+      if (idx < BK * TBN) {
+        const int c = idx % TBN, k = idx / TBN;
+        const int64_t gk = k0 + k;
+        const int gc = c0 + c;
+        Bs[k][c] = (gk < kend && gc < s) ? B[gk * s + gc] : 0.0;
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[TJ];
+      double a[2], b[TJ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+      for (int i = 0; i < 2; ++i) a[i] = As[k][ty * 2 + i];
 #pragma unroll
-      for (int j = 0; j < TJ; ++j) b[j] = Bs[k][tx + 16 * j];
+      for (int j = 0; j < TJ; ++j) b[j] = Bs[k][tx + 8 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < TJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t gm = m0 + ty * 4 + i;
+  for (int i = 0; i < 2; ++i) {
+    const int64_t gm = m0 + ty * 2 + i;
     if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < TJ; ++j) {
-      const int gc = c0 + tx + 16 * j;
+      const int gc = c0 + tx + 8 * j;
       if (gc < s) C[gm * s + gc] = acc[i][j];
     }
   }
@@ -169,12 +175,12 @@ int sm_count() {
   return sms > 0 ? sms : 152;
 }
 
-// Columns per thread of the product's tile: 16 TJ >= s up to TJ = 8 (wider s: tiles of 128).
-int col_per_thread(int s) { return std::min(8, std::max(1, (s + 15) / 16)); }
+// Column slots per thread of the product's tile: 8 TJ >= s up to TJ = 16 (wider s: tiles of 128).
+int col_per_thread(int s) { return std::min(16, std::max(1, (s + 7) / 8)); }
 
 // Slices of the reduction and their length (a multiple of BK) for an M x K product.
 void plan_slices(int64_t M, int64_t K, int s, int* nslices, int64_t* kslice) {
-  const int tbn = 16 * col_per_thread(s);
+  const int tbn = 8 * col_per_thread(s);
   const int64_t tiles = ((M + BM - 1) / BM) * ((s + tbn - 1) / tbn);
   const int slices = reduction_slices(K, tiles, sm_count());
   *kslice = ((K + slices - 1) / slices + BK - 1) / BK * BK;
@@ -193,7 +199,7 @@ void launch_tj(bool trans, const dim3& grid, cudaStream_t st, const double* A, i
 cudaError_t launch_slices(bool trans, const double* A, int64_t lda, int64_t M, int64_t K,
                           const double* B, int s, double* C, int nslices, int64_t kslice,
                           int64_t ldc, cudaStream_t st) {
-  const int tj = col_per_thread(s), tbn = 16 * tj;
+  const int tj = col_per_thread(s), tbn = 8 * tj;
   const dim3 grid(static_cast<unsigned>((M + BM - 1) / BM), static_cast<unsigned>((s + tbn - 1) / tbn),
                   static_cast<unsigned>(nslices));
   switch (tj) {
@@ -204,7 +210,15 @@ cudaError_t launch_slices(bool trans, const double* A, int64_t lda, int64_t M, i
     case 5: launch_tj<5>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
     case 6: launch_tj<6>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
     case 7: launch_tj<7>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
-    default: launch_tj<8>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 8: launch_tj<8>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 9: launch_tj<9>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 10: launch_tj<10>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 11: launch_tj<11>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 12: launch_tj<12>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 13: launch_tj<13>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 14: launch_tj<14>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    case 15: launch_tj<15>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
+    default: launch_tj<16>(trans, grid, st, A, lda, M, K, B, s, C, kslice, ldc); break;
   }
   return cudaGetLastError();
 }
