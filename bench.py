@@ -37,8 +37,8 @@ UNIT = "N*s/s"
 N_DEF, R_DEF, S_DEF, LEAF_DEF, SEED = 32768, 40, 120, 64, 220502990 + 200
 SM_COUNT_GB300 = 152
 FP64_DFMA_PER_CLK_PER_SM = 2          # GB300: FP64 at 1/64 of the FP32 rate (1.25 TF nominal)
-GEMM_READ_8192 = 549.46e6             # dram bytes read by one sample_gemm_f64 launch, N = 8192
-GEMM_WRITE_8192 = 42.30e6             # dram bytes written (split-K partials) by that launch
+GEMM_READ_8192 = 549.24e6             # dram bytes read by one sample_gemm_f64 launch, N = 8192
+GEMM_WRITE_8192 = 41.77e6             # dram bytes written (split-K partials) by that launch
 def measured_peaks():
     """Dense bf16 (sustained) and HBM copy peaks measured on the GB300s
     (MEASURED_PEAKS.json beside this file, written by the pool's driver), else the fallback of one
