@@ -8,7 +8,7 @@ magnitude and each dropped pair weighs at most 6 * 2^-38 of the product of the b
 an output entry errs by ~2^-36 times sum_k (max|a| max|b|) over its windows; for these inputs the
 block maxima are within ~30x of the typical entries, hence the bounds below: 1e-9 of
 sum_k |a_k b_k| per entry, 1e-10 relative Frobenius (measured 0.8e-12 .. 2.7e-12 per entry,
-7e-12 .. 1.4e-11 Frobenius).
+7.4e-12 .. 2.0e-11 Frobenius).
 
 Sweep: the LQ of each test block and the bases in FP64, D_tau and the merges in double-float
 (FP32 pairs, ~2^-48 per operation). Factors are held to the FP64 bar, 1e-10, against the oracle
