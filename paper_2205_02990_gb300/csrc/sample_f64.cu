@@ -308,11 +308,13 @@ cudaError_t launch_sample_dense_f64(const double* A, int64_t lda, int64_t N, con
 cudaError_t launch_sample_host_f64(const double* A, int64_t lda, int64_t N, const double* Om,
                                    const double* Ps, int s, double* Y, double* Z,
                                    cudaStream_t st) {
-  // Row blocks (multiples of the 64-row tile) doubling from ~N/32 rows up to ~N/8 rows (at most
+  // Row blocks (multiples of the 64-row tile) doubling from ~N/32 rows up to ~N/4 rows (at most
   // 2 GiB of staging each): the first copy, which nothing hides, stays short, and few blocks are
-  // small (a small block's products fill the GPU less well).
+  // small (a small block's products fill the GPU less well: at N = 32768 the streamed products
+  // took 456, 427 and 424 ms with blocks of up to N/16, N/8 and N/4 rows, against 416 ms from
+  // device memory).
   const int64_t cap = std::max<int64_t>(BM, (int64_t(1) << 28) / std::max<int64_t>(1, N) / BM * BM);
-  const int64_t nb_max = std::min(N, std::max<int64_t>(BM, std::min(((N + 7) / 8 + BM - 1) / BM * BM, cap)));
+  const int64_t nb_max = std::min(N, std::max<int64_t>(BM, std::min(((N + 3) / 4 + BM - 1) / BM * BM, cap)));
   std::vector<int64_t> rows_of;
   std::vector<int> zs_of;
   int64_t total_slices = 0;
