@@ -100,7 +100,17 @@ def sweep_flops(N, r, s, leaf):
 # S - op(D) T and the two basis products per pass) or as the reduced finishes do (D with U^* D
 # and (D V)^*, then [B^*, -H][S; T]).
 def side_flops(n, s):
-    return 2 * n * n * (s - n / 3) + (4 * n * n * s - 2 * n ** 3) + n ** 3
+    return side_lq_flops(n, s) + side_rows_flops(n, s)
+
+
+def side_lq_flops(n, s):
+    """The LQ of one n x s test block."""
+    return 2 * n * n * (s - n / 3)
+
+
+def side_rows_flops(n, s):
+    """Its n sample rows through the n reflectors, and the back substitution."""
+    return (4 * n * n * s - 2 * n ** 3) + n ** 3
 
 
 def bases_flops(n, r):
@@ -356,7 +366,8 @@ MODES = {
                  what="FP64 products on the FP64 pipe + FP64 sweep"),
     "mixed": dict(sample=2, sweep=2, a="f32",
                   what="A stored FP32; bf16x6 products on tcgen05 tensor cores; sweep with FP64 "
-                       "nullspace QR / pseudo-inverse and FP32 bases, D_tau and merges"),
+                       "nullspace LQ / pseudo-inverse (sample rows through it in double-float) and "
+                       "FP32 bases, D_tau and merges"),
     "tc64": dict(sample=2, sweep=0, a="f32",
                  what="A stored FP32; bf16x6 products on tcgen05 tensor cores; FP64 sweep"),
     "oz64": dict(sample=3, sweep=3, a="f64",
@@ -368,10 +379,11 @@ MODES = {
                      "per 64 x 64 block of A (15 FP16 digit-pair products on tcgen05 tensor cores, "
                      "exact FP32 sums); sweep with "
                      "FP64 nullspace LQ / pseudo-inverse and bases, double-float (compensated "
-                     "FP32) D_tau and merges"),
+                     "FP32) sample rows through the LQ, D_tau and merges"),
     "mixed3": dict(sample=1, sweep=1, a="f32",
                    what="A stored FP32; bf16x3 products on tcgen05 tensor cores; sweep with FP64 "
-                        "nullspace QR / pseudo-inverse and FP32 bases, D_tau and merges"),
+                        "nullspace LQ / pseudo-inverse (sample rows through it in double-float) "
+                        "and FP32 bases, D_tau and merges"),
 }
 FINISH = {0: "fp64", 1: "fp32", 2: "fp32", 3: "fp64", 4: "df32"}
 
@@ -389,27 +401,67 @@ def peaks_now(hb):
             "mma_issue_cycles": hb.hbs_probe_mma_issue()}
 
 
-def sweep_roofline(phase_ms, N, r, s, leaf, finish, peaks):
+def side_split_per_height(N, r, s, leaf):
+    """Per height (finest first): (LQ flops, sample-row flops, largest node) of the side phase."""
+    L = tree_nodes(N, leaf)
+    out = []
+    for level in range(L, -1, -1):
+        cnt = 2 ** level
+        if level == L and L > 0:
+            big, small = -(-N // cnt), N // cnt
+            groups = [(big, N - small * cnt), (small, cnt - (N - small * cnt))]
+        elif level == 0:
+            groups = [(2 * r if L > 0 else N, 1)]
+        else:
+            groups = [(2 * r, cnt)]
+        sides = 1 if level == 0 else 2
+        out.append((sum(c * sides * side_lq_flops(n, s) for n, c in groups),
+                    sum(c * sides * side_rows_flops(n, s) for n, c in groups),
+                    max(n for n, _ in groups)))
+    return out
+
+
+def sweep_roofline(phase_ms, N, r, s, leaf, finish, peaks, tuning=None):
     """Roofline of the sweep's four phases from a hbs_profile_sweep run: algorithmic flops
     (sweep_phase_flops) per height and phase over the CUDA-event time, against the derived peak
     of the pipe each phase runs on (FP64; FP32 for the plain mixed finish; double-float: the FP32
-    peak over the 15 FP32 instructions of one double-float multiply-add)."""
+    peak over the 15 FP32 instructions of one double-float multiply-add). With a reduced finish
+    the side phase runs its LQ in FP64 and, at heights of the one-CTA form (tuning R > 0), its
+    sample rows in double-float: its fraction is then the time those flops need at their pipes'
+    peaks over the measured time."""
     flops = sweep_phase_flops(N, r, s, leaf, False if finish == "fp64" else finish)
     names = ("side", "bases", "D", "merge")
     pipe = {"side": "fp64", "bases": "fp32" if finish == "fp32" else "fp64",
             "D": finish, "merge": finish}
     peak = {p: peaks[p + "_derived"] for p in ("fp64", "fp32", "df32")}
+    # the side phase's ideal time per height (s), by pipe
+    split = side_split_per_height(N, r, s, leaf)
+    side_ideal = []
+    for h, (lq, rows, nmax) in enumerate(split):
+        df_rows = (finish != "fp64" and tuning is not None and h < len(tuning) and tuning[h] > 0
+                   and (finish == "fp32" or df32_fits(nmax, r)))
+        side_ideal.append(lq / (peak["fp64"] * 1e12)
+                          + rows / ((peak["df32"] if df_rows else peak["fp64"]) * 1e12))
+    if finish != "fp64":
+        pipe["side"] = "fp64 LQ + df32 sample rows (one-CTA heights)"
     per_kernel = {}
     for k, nm in enumerate(names):
         ms = sum(h[k] for h in phase_ms)
         fl = sum(f[k] for f in flops)
         ach = fl / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+        if nm == "side" and finish != "fp64":
+            frac = sum(side_ideal) / (ms * 1e-3) if ms > 0 else 0.0
+            fbh = [round(t / (h[0] * 1e-3), 3) if h[0] > 0 else None
+                   for h, t in zip(phase_ms, side_ideal)]
+            pk = None
+        else:
+            frac = ach / peak[pipe[nm]]
+            fbh = [round((f[k] / (h[k] * 1e-3) / 1e12) / peak[pipe[nm]], 3)
+                   if h[k] > 0 and f[k] > 0 else None for h, f in zip(phase_ms, flops)]
+            pk = peak[pipe[nm]]
         per_kernel[nm] = {"ms": ms, "gflop": fl / 1e9, "achieved_tflops": ach,
-                          "pipe": pipe[nm], "peak_tflops": peak[pipe[nm]],
-                          "frac": ach / peak[pipe[nm]],
-                          "frac_by_height": [round((f[k] / (h[k] * 1e-3) / 1e12) / peak[pipe[nm]], 3)
-                                             if h[k] > 0 and f[k] > 0 else None
-                                             for h, f in zip(phase_ms, flops)],
+                          "pipe": pipe[nm], "peak_tflops": pk, "frac": frac,
+                          "frac_by_height": fbh,
                           "ms_by_height": [round(h[k], 4) for h in phase_ms]}
     tot_ms = sum(sum(h) for h in phase_ms)
     tot_fl = sum(sum(f) for f in flops)
@@ -842,7 +894,8 @@ def main():
                     elapsed=elapsed, elapsed_plain=elapsed_plain, per_launch=per_launch,
                     products_ms=products_ms, clocks=clk.summary() if clk else None,
                     tuning=hb.hbs_get_tuning(h),
-                    sweep=sweep_roofline(phases, N, r, s, leaf, FINISH[cfg["sweep"]], peaks))
+                    sweep=sweep_roofline(phases, N, r, s, leaf, FINISH[cfg["sweep"]], peaks,
+                                         hb.hbs_get_tuning(h)))
 
     def power_norm(apply_B, apply_Bt, steps=20):
         g = torch.Generator(device="cuda").manual_seed(3)

@@ -74,7 +74,8 @@ typedef enum {
                                entry of its block, so a row or column far below the rest of its
                                block loses relative accuracy (the products' normwise error is
                                unaffected); about 10 N^2 bytes of scratch. Sweep: the LQ of each test block
-                               (nullspace, pseudo-inverse) and the bases in FP64, D_tau and the
+                               (nullspace, pseudo-inverse) and the bases in FP64, the sample
+                               rows pushed through the LQ (see hbs_plan), D_tau and the
                                parent blocks in double-float arithmetic (pairs of FP32 numbers,
                                ~48 significant bits, FP32 exponent range: every intermediate
                                of those products must stay within about 1e-30 .. 1e38 in
@@ -173,8 +174,10 @@ typedef struct hbs_handle hbs_handle;   /* opaque: owns the factors and all work
  * n (s + 1) + 2n doubles; the basis tile, r (n + 1) + n (r + 1) + 10 r doubles (floats with
  * HBS_PREC_MIXED_BF16X3/X6); the reduced-precision D tile below.
  * Sweep precision: HBS_PREC_FP64 and HBS_PREC_FP64_TC keep every step in FP64; every other
- * precision keeps the LQ of each test block (nullspace and pseudo-inverse) and the sample rows
- * pushed through it in FP64; HBS_PREC_MIXED_BF16X3/X6 compute the bases, D_tau and the parent
+ * precision keeps the LQ of each test block (nullspace and pseudo-inverse) in FP64 and pushes
+ * the sample rows through it in double-float where a height runs the one-CTA side form (in FP64
+ * where it runs the cluster form; a height that falls back to the FP64 finish, below, streams
+ * in FP64); HBS_PREC_MIXED_BF16X3/X6 compute the bases, D_tau and the parent
  * blocks in FP32, HBS_PREC_MIXED_COMPENSATED the bases in FP64 and D_tau and the parent blocks
  * in double-float (factors stored in FP64). The D and merge tiles of the reduced finishes take
  * r (n + 1) + 3 n r + n (n + 1) + n^2 values (4-byte floats, or 8-byte pairs); a tree height

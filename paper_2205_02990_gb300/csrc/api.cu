@@ -1136,20 +1136,29 @@ int hbs_autotune(hbs_handle* h, void* cuda_stream) {
     const int ntasks = int(H.tasks.size());
     float best_ms = 1e30f;
     int best = hbs::side_row_splits(ntasks, H.max_n, H.max_s);
+    // With a reduced finish (FP32 or double-float) the one-CTA form streams the sample rows in
+    // double-float and the cluster form in FP64, so the tuner keeps the automatic form there
+    // (every shape within a form rounds alike; the factors of a tuned run equal the automatic
+    // ones).
+    const bool df = hbs::effective_finish(H.max_n, H.max_r, finish_of(h->precision)) != hbs::kFinishF64;
+    const int form = best > 0 ? 1 : -1;
     // row slices (each CTA factors the test block) and clusters of C CTAs sharing one
     // factorization (R = -C)
     for (int R : {1, 2, 3, 4, 6, 8, 12, 16, -1, -2, -3, -4, -6, -8}) {
       if (std::abs(R) > std::max(1, H.max_n / 8)) continue;
       if (R < 0 && !hbs::side_cluster_fits(H.max_n, H.max_s, -R)) continue;
+      if (df && R * form < 0) continue;
       // one untimed launch, then the mean of three
-      cudaError_t e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st);
+      cudaError_t e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st,
+                                            nullptr, df);
       if (R < 0 && e != cudaSuccess && e != cudaErrorLaunchFailure) {
         cudaGetLastError();                            // a cluster shape the GPU cannot place
         continue;
       }
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
       for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-        e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st);
+        e = hbs::launch_side_only(H.d_tasks, ntasks, H.max_n, H.max_s, R, h->d_status, st,
+                                  nullptr, df);
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;

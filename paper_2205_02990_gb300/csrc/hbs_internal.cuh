@@ -102,9 +102,11 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
                                FinishShape shape = FinishShape{}, const double* lq = nullptr);
 // The side kernel of one height alone (for tuning; idempotent). R > 0: R row slices per
 // (node, side), each CTA factoring the test block (or copying it from lq); R < 0: a cluster of
-// -R CTAs per (node, side) sharing one factorization.
+// -R CTAs per (node, side) sharing one factorization. df: the one-CTA form streams the sample
+// rows in double-float (the reduced finishes; the cluster form streams in FP64 either way).
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
-                             int R, int* d_status, cudaStream_t st, const double* lq = nullptr);
+                             int R, int* d_status, cudaStream_t st, const double* lq = nullptr,
+                             bool df = false);
 // The LQ of every test block of a height (both sides), written to lq: 2 ntasks images of
 // side_lq_stride(max_n, max_s) doubles, (node, side) at (2 node + side) * stride.
 cudaError_t launch_side_lq(const NodeTask* d_tasks, int ntasks, int max_n, int max_s, double* lq,

@@ -8,7 +8,9 @@
 //   V^* Omega_tau, U^* Psi_tau, U^* (Y_tau - D Omega_tau), V^* (Z_tau - D^* Psi_tau).
 // At the root only D = Y Omega^+ (Section 4.3).
 //
-// Side kernel (FP64 in every precision: it holds the nullspace and the pseudo-inverse); side 0
+// Side kernel (the LQ in FP64 in every precision: it holds the nullspace and the pseudo-inverse;
+// with the reduced finishes the one-CTA form pushes the sample rows through it in double-float,
+// the cluster form in FP64); side 0
 // works on Omega_tau and Y_tau, side 1 on Psi_tau and Z_tau. One Householder LQ of the test
 // block, Omega_tau = L Q^* (the QR of Omega_tau^* of Section 2.4, Q square), serves both `null`
 // and the pseudo-inverse: the last r columns of Q are null(Omega_tau, r), and
@@ -247,6 +249,117 @@ __device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, i
   }
 }
 
+// ---- the same streaming in double-float (compensated finish, single-CTA side form) -----------
+// The LQ stays FP64; its shared-memory image (reflectors with L_1 below the diagonal, tau, 1/beta)
+// is then converted in place to double-float pairs, and the sample rows go through it on the
+// FP32 pipe: a double-float multiply-add is ~15 FP32 instructions against one FP64 instruction
+// that holds the FP64 unit as long as 64 FP32 ones on GB300.
+
+// Sum over the 8 lanes of a row group (butterfly: every lane ends with the same bits).
+__device__ __forceinline__ dfloat df_group_sum(dfloat v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const dfloat w{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+template <int NS>
+__device__ __forceinline__ void apply_reflector_df(dfloat (&y)[NS], const dfloat* v, dfloat tj, int j,
+                                                   int cols, int q) {
+  dfloat part = df_zero();
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    if (G * t + G - 1 < j || G * t >= cols) continue;
+    const int k = q + G * t;
+    const dfloat vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : df_zero();
+    part = df_fma_acc(y[t], vk, part);
+  }
+  const dfloat w = df_neg(df_fma(df_group_sum(df_norm(part)), tj, df_zero()));
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    if (G * t + G - 1 < j || G * t >= cols) continue;
+    const int k = q + G * t;
+    const dfloat vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : df_zero();
+    y[t] = df_fma(w, vk, y[t]);
+  }
+}
+
+// store_row in double-float: the last r entries to X, then the back substitution against L_1
+// and the first n entries to W (both stored as FP64).
+template <int NS>
+__device__ __forceinline__ void store_row_df(dfloat (&y)[NS], int i, bool active, int n, int s, int r,
+                                             const dfloat* F, int ldF, const dfloat* rdiag,
+                                             double* __restrict__ X, double* __restrict__ W) {
+  const int q = threadIdx.x % G;
+  const int gbase = (threadIdx.x % 32) & ~(G - 1);
+  if (X != nullptr && active) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      if (k >= s - r && k < s) X[static_cast<size_t>(i) * r + (k - (s - r))] = df_to(y[t]);
+    }
+  }
+#pragma unroll
+  for (int t = NS - 1; t >= 0; --t) {
+    if (G * t >= n) continue;
+#pragma unroll 1
+    for (int qq = G - 1; qq >= 0; --qq) {
+      const int j = qq + G * t;
+      if (j >= n) continue;
+      const dfloat yj{__shfl_sync(FULL, y[t].hi, gbase + qq), __shfl_sync(FULL, y[t].lo, gbase + qq)};
+      const dfloat wj = df_fma(yj, rdiag[j], df_zero());
+      if (q == qq) y[t] = wj;
+      const dfloat nwj = df_neg(wj);
+      const dfloat* Lj = F + static_cast<size_t>(j) * ldF;
+#pragma unroll
+      for (int tt = 0; tt <= t; ++tt) {
+        const int k = q + G * tt;
+        if (k < j) y[tt] = df_fma(nwj, Lj[k], y[tt]);
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      if (k < n) W[static_cast<size_t>(i) * n + k] = df_to(y[t]);
+    }
+  }
+}
+
+template <int NS>
+__device__ void stream_rows_df(const double* __restrict__ S, int n, int s, int r, int row0, int row1,
+                               const dfloat* F, int ldF, const dfloat* tau, const dfloat* rdiag,
+                               double* __restrict__ X, double* __restrict__ W) {
+  const int gid = threadIdx.x / G, q = threadIdx.x % G;
+  for (int base = row0; base < row1; base += NGROUPS) {
+    if (base + (threadIdx.x / 32) * (32 / G) >= row1) break;   // no row for this warp
+    const int i = base + gid;
+    const bool active = i < row1;
+    dfloat y[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      const int k = q + G * t;
+      y[t] = (active && k < s) ? df_from(S[static_cast<size_t>(i) * s + k]) : df_zero();
+    }
+    for (int j = 0; j < n; ++j)
+      apply_reflector_df<NS>(y, F + static_cast<size_t>(j) * ldF, tau[j], j, s, q);
+    store_row_df<NS>(y, i, active, n, s, r, F, ldF, rdiag, X, W);
+  }
+}
+
+// The side kernel's shared-memory image (len values) from FP64 to double-float, in place.
+__device__ __forceinline__ void image_to_df(double* img, int len) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < len; e += THREADS) {
+    const dfloat v = df_from(img[e]);
+    reinterpret_cast<dfloat*>(img)[e] = v;
+  }
+  __syncthreads();
+}
+
 // Basis B (n x r, leading dimension ldB, FP64 storage) = first r columns of H_0 ... H_{r-1},
 // the reflectors of the LQ of XT (r x n) -- i.e. col(X, r) for X = XT^*. Backward accumulation
 // on an n x r tile W in shared memory: W = [I_r; 0], then W <- H_j W for j = r-1 .. 0. H_j acts
@@ -297,7 +410,8 @@ __device__ void form_basis(const Real* XT, int ldX, const Real* tau2, int r, int
 // PRE: the factorization of the test block was made beforehand by node_lq (its shared-memory
 // image in `lq`, lq_stride doubles per (node, side)) and is copied in instead of recomputed;
 // the same instructions made it, so the results are bit-identical.
-template <int NS, int MINB, bool PRE = false>
+// DF: the sample rows stream in double-float (compensated finish).
+template <int NS, int MINB, bool PRE = false, bool DF = false>
 __global__ void __launch_bounds__(THREADS, MINB)
     node_side(const NodeTask* __restrict__ tasks, int row_splits, int* status,
               const double* __restrict__ lq = nullptr, int64_t lq_stride = 0) {
@@ -324,12 +438,25 @@ __global__ void __launch_bounds__(THREADS, MINB)
     __syncthreads();
     lq_factor<double>(F, ldF, n, s, tau, rdiag, status);
   }
-  if (tk.is_root) {
-    stream_rows<NS>(tk.Y, n, s, 0, row0, row1, F, ldF, tau, rdiag, nullptr, tk.D);
-    return;
+  if constexpr (DF) {
+    image_to_df(F, n * ldF + 2 * n);
+    const dfloat* Fd = reinterpret_cast<const dfloat*>(F);
+    const dfloat* taud = Fd + static_cast<size_t>(n) * ldF;
+    const dfloat* rdiagd = taud + n;
+    if (tk.is_root) {
+      stream_rows_df<NS>(tk.Y, n, s, 0, row0, row1, Fd, ldF, taud, rdiagd, nullptr, tk.D);
+      return;
+    }
+    stream_rows_df<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, Fd, ldF, taud, rdiagd,
+                       side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
+  } else {
+    if (tk.is_root) {
+      stream_rows<NS>(tk.Y, n, s, 0, row0, row1, F, ldF, tau, rdiag, nullptr, tk.D);
+      return;
+    }
+    stream_rows<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, F, ldF, tau, rdiag,
+                    side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
   }
-  stream_rows<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, F, ldF, tau, rdiag,
-                  side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
 }
 
 // The LQ of one test block alone (grid: node, side), its shared-memory image (F, tau, 1/beta:
@@ -994,7 +1121,7 @@ cudaError_t launch_side_lq(const NodeTask* d_tasks, int ntasks, int max_n, int m
 // test block itself (or, with lq, copying the factorization node_lq left there); R < 0: a
 // cluster of -R CTAs per (node, side) sharing one factorization (lq must be NULL).
 cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int max_s,
-                             int R, int* d_status, cudaStream_t st, const double* lq) {
+                             int R, int* d_status, cudaStream_t st, const double* lq, bool df) {
   if (ntasks <= 0) return cudaSuccess;
   if (max_s > kMaxS) return cudaErrorInvalidValue;
   if (lq != nullptr && R < 0) return cudaErrorInvalidValue;
@@ -1039,23 +1166,28 @@ cudaError_t launch_side_only(const NodeTask* d_tasks, int ntasks, int max_n, int
       e = cudaGetLastError();
     }
   };
-  auto pick = [&](auto pre) {
-    constexpr bool P = decltype(pre)::value;
+  auto pick = [&](auto pre, auto dfl) {
+    constexpr bool P = decltype(pre)::value, D = decltype(dfl)::value;
     if (max_s <= 8 * G) {
-      if (fit >= 4) side(node_side<8, 4, P>);
-      else if (fit == 3) side(node_side<8, 3, P>);
-      else side(node_side<8, 2, P>);
+      if (fit >= 4) side(node_side<8, 4, P, D>);
+      else if (fit == 3) side(node_side<8, 3, P, D>);
+      else side(node_side<8, 2, P, D>);
     } else if (max_s <= 16 * G) {
-      if (fit >= 4) side(node_side<16, 4, P>);
-      else if (fit == 3) side(node_side<16, 3, P>);
-      else side(node_side<16, 2, P>);
+      if (fit >= 4) side(node_side<16, 4, P, D>);
+      else if (fit == 3) side(node_side<16, 3, P, D>);
+      else side(node_side<16, 2, P, D>);
     } else {
-      if (fit >= 3) side(node_side<24, 3, P>);
-      else side(node_side<24, 2, P>);
+      if (fit >= 3) side(node_side<24, 3, P, D>);
+      else side(node_side<24, 2, P, D>);
     }
   };
-  if (lq != nullptr) pick(std::true_type{});
-  else pick(std::false_type{});
+  if (lq != nullptr) {
+    if (df) pick(std::true_type{}, std::true_type{});
+    else pick(std::true_type{}, std::false_type{});
+  } else {
+    if (df) pick(std::false_type{}, std::true_type{});
+    else pick(std::false_type{}, std::false_type{});
+  }
   return e;
 }
 
@@ -1088,7 +1220,7 @@ cudaError_t launch_sweep_level(const NodeTask* d_tasks, int ntasks, int max_n, i
   cudaError_t e = mark(0);
   if (e == cudaSuccess)
     e = launch_side_only(d_tasks, ntasks, max_n, max_s, side_shape(ntasks, max_n, max_s, row_splits),
-                         d_status, st, lq);
+                         d_status, st, lq, reduced);
   if (e == cudaSuccess) e = mark(1);
   if (e != cudaSuccess) return e;
   // bases: one CTA per (node, side); the register slots span the n <= s columns of a basis
