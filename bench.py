@@ -1043,10 +1043,12 @@ def main():
         # splits + 2 GEMMs + 2 reductions; digits: 2 test-matrix splits + 1 A split + 2 GEMMs +
         # 2 reductions), then per tree level the side, bases, D and merge kernels (FP64: D in two
         # kernels; FP32: one)
-        # (+ node_lq, the leaves' LQ, where the leaf height runs the one-CTA side form)
+        # (+ node_lq, the leaves' LQ, where the leaf height runs the one-CTA side form of an
+        # FP64 sweep)
         "gpu_launches": args.steps * ({0: 2 + 2 + 2, 1: 2 + 6, 2: 2 + 6, 3: 2 + 3 + 4,
                                        4: 2 + 3 + 4}[MODES[head]["sample"]]
-                                      + (1 if res["tuning"][0] > 0 else 0)
+                                      + (1 if res["tuning"][0] > 0 and FINISH[MODES[head]["sweep"]] == "fp64"
+                                         else 0)
                                       + sweep_launches(N, r, s, leaf, res["tuning"],
                                                        MODES[head]["sweep"] in (1, 2, 4))),
         "roofline": dict(roofline, sweep=res["sweep"]),

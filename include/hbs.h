@@ -207,7 +207,9 @@ int hbs_compress(int32_t batch, const hbs_problem* probs, int32_t precision, hbs
  * stream priority) from the draws on, and `cuda_stream` waits for it before the sweep. The
  * leaf level's side kernel then takes those factorizations instead of computing them: the
  * factors are bit-identical to hbs_sample + hbs_execute. Where the leaf height runs the cluster
- * form of the side kernel (a tree with few leaves) nothing is overlapped.
+ * form of the side kernel (a tree with few leaves), or a reduced sweep precision streams the
+ * leaves' sample rows in double-float (there the fused side kernel is faster), nothing is
+ * overlapped and the call equals hbs_sample + hbs_execute.
  * probs->Omega, Psi, Y and Z are written (writable device buffers, N x s FP64 row-major).
  * op->N must equal probs->N; the operator rules are hbs_sample's. The handle's second stream
  * and its image buffer (2 leaves (n (s + 1) + 2 n) doubles for leaves of n rows) are made on

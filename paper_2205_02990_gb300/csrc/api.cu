@@ -715,11 +715,15 @@ int bind_problems(hbs_handle* h, const hbs_problem* probs, cudaStream_t st, cons
   return HBS_OK;
 }
 
-// The leaf height can take its factorizations from node_lq when it runs the one-CTA side form.
+// The leaf height takes its factorizations from node_lq when it runs the one-CTA side form with
+// FP64 sample rows. (With a reduced finish the rows stream in double-float, and the fused side
+// kernel, 2.06 ms at the leaves of the N = 32768 log-kernel tree, beats node_lq + the copying
+// kernel, 1.20 + 1.02 ms, which the products leave no room to overlap.)
 bool leaves_prefactorable(const hbs_handle* h) {
   if (h->items.size() != 1 || h->items[0].L < 1 || h->heights.empty()) return false;
   const Height& H = h->heights[0];
-  return hbs::side_shape(int(H.tasks.size()), H.max_n, H.max_s, H.R) > 0;
+  return hbs::side_shape(int(H.tasks.size()), H.max_n, H.max_s, H.R) > 0 &&
+         hbs::effective_finish(H.max_n, H.max_r, finish_of(h->precision)) == hbs::kFinishF64;
 }
 
 // lq_buf, the second stream (the highest priority, so that its CTAs are placed among the
