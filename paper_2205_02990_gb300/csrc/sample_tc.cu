@@ -49,19 +49,39 @@ constexpr int BM = 128;                       // MMA M: rows of C per CTA
 constexpr int BK = 64;                        // reduction columns per stage (128 B of bf16)
 constexpr int kSliceABytes = BM * BK * 2;     // one bf16 slice of the A tile
 constexpr int kUnitsPerThread = BM * BK / 8 / (32 * kConvWarps);   // (row, 8-column) units
-// One converter thread's units of the A tile (rows m0.., reduction columns k0..): unit u is
-// (row m, 8-column chunk c) of op(A); the thread holds its 8 FP32 values. Y = A Omega reads
-// A[m0 + m][k0 + 8c ..] (8 lanes cover one 256-byte row); Z = A^* Psi reads A[k0 + 8c + e][m0 + m]
-// (32 lanes read 32 consecutive m of one row of A). Entries outside M x K read as zero.
+static_assert(kUnitsPerThread == 4, "the Z mapping gives a thread 4 neighbouring rows of op(A)");
+// Unit `it` of converter thread ct is (row m, 8-column chunk c) of op(A); the thread holds its 8
+// FP32 values. Y = A Omega: u = ct + 256 it, m = u / 8, c = u % 8 (8 lanes cover one 256-byte row
+// of A). Z = A^* Psi: the thread's 4 units are 4 neighbouring columns of A (m = 4 mb + it), read
+// as one 16-byte vector per row of A; lane l of warp w takes c = l % 4 + 4 (w % 2) and
+// mb = l / 4 + 8 (w / 2), so that a warp reads whole 128-byte lines (4 rows of A, 32 columns)
+// and the 8 lanes of a shared-memory store phase write two rows of the tile whose m % 8 differ
+// in bit 2 (8 distinct swizzled chunks: no bank conflict).
+template <bool TRANS>
+__device__ __forceinline__ void unit_coords(int ct, int it, int& m, int& c) {
+  if (!TRANS) {
+    const int u = ct + 32 * kConvWarps * it;
+    m = u >> 3;
+    c = u & 7;
+  } else {
+    const int w = ct >> 5, l = ct & 31;
+    m = 4 * ((l >> 2) + 8 * (w >> 1)) + it;
+    c = (l & 3) + 4 * (w & 1);
+  }
+}
+
+// Loads the thread's units of the A tile (rows m0.., reduction columns k0..). Y reads
+// A[m0 + m][k0 + 8c ..] as two float4; Z reads, for each e < 8, A[k0 + 8c + e][m0 + 4 mb ..]
+// as one float4. A is 16-byte aligned and lda % 4 == 0. Entries outside M x K read as zero.
 template <bool TRANS>
 __device__ __forceinline__ void load_units(const float* __restrict__ A, int64_t lda, int M, int K,
                                            int m0, int k0, int ct,
                                            float (&v)[kUnitsPerThread][8]) {
+  if (!TRANS) {
 #pragma unroll
-  for (int it = 0; it < kUnitsPerThread; ++it) {
-    const int u = ct + 32 * kConvWarps * it;
-    if (!TRANS) {
-      const int m = u >> 3, c = u & 7;
+    for (int it = 0; it < kUnitsPerThread; ++it) {
+      int m, c;
+      unit_coords<false>(ct, it, m, c);
       const int64_t gm = m0 + m, gk = k0 + 8 * c;
       if (gm < M && gk + 8 <= K) {
         const float4* q = reinterpret_cast<const float4*>(A + gm * lda + gk);
@@ -72,13 +92,20 @@ __device__ __forceinline__ void load_units(const float* __restrict__ A, int64_t 
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[it][e] = (gm < M && gk + e < K) ? A[gm * lda + gk + e] : 0.f;
       }
-    } else {
-      const int m = u & (BM - 1), c = u >> 7;
-      const int64_t gm = m0 + m;
+    }
+  } else {
+    int m, c;
+    unit_coords<true>(ct, 0, m, c);
+    const int64_t gm = m0 + m;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int64_t gk = k0 + 8 * c + e;
-        v[it][e] = (gm < M && gk < K) ? A[gk * lda + gm] : 0.f;
+    for (int e = 0; e < 8; ++e) {
+      const int64_t gk = k0 + 8 * c + e;
+      if (gk < K && gm + 4 <= M) {
+        const float4 q = *reinterpret_cast<const float4*>(A + gk * lda + gm);
+        v[0][e] = q.x; v[1][e] = q.y; v[2][e] = q.z; v[3][e] = q.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i][e] = (gk < K && gm + i < M) ? A[gk * lda + gm + i] : 0.f;
       }
     }
   }
@@ -112,9 +139,8 @@ __device__ __forceinline__ void store_units(const float (&v)[kUnitsPerThread][8]
                                             int ct) {
 #pragma unroll
   for (int it = 0; it < kUnitsPerThread; ++it) {
-    const int u = ct + 32 * kConvWarps * it;
-    const int m = TRANS ? (u & (BM - 1)) : (u >> 3);
-    const int c = TRANS ? (u >> 7) : (u & 7);
+    int m, c;
+    unit_coords<TRANS>(ct, it, m, c);
     uint32_t w[P][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
