@@ -277,8 +277,9 @@ def hbs_execute(handle, problems=None):
 
 
 def hbs_sample_execute(handle, A, seed, precision=HBS_PREC_FP64, problems=None, N=None):
-    """hbs_sample into the problem's Omega, Psi, Y, Z, then hbs_execute, with the leaves'
-    test-block LQ on a second stream while the products run (a one-problem handle)."""
+    """hbs_sample into the problem's Omega, Psi, Y, Z, then hbs_execute (a one-problem
+    handle); with an FP64 sweep the leaves' test-block LQ runs on a second stream while the
+    products run."""
     problems = handle.problems if problems is None else list(problems)
     op, keep, _ = _operator(A, problems[0].N if N is None else N)
     _check(load().hbs_sample_execute(handle.ptr, ctypes.byref(op), seed, precision,
