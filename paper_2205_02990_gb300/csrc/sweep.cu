@@ -253,7 +253,9 @@ __device__ void stream_rows(const double* __restrict__ S, int n, int s, int r, i
 // The LQ stays FP64; its shared-memory image (reflectors with L_1 below the diagonal, tau, 1/beta)
 // is then converted in place to double-float pairs, and the sample rows go through it on the
 // FP32 pipe: a double-float multiply-add is ~15 FP32 instructions against one FP64 instruction
-// that holds the FP64 unit as long as 64 FP32 ones on GB300.
+// that holds the FP64 unit as long as 64 FP32 ones on GB300. Where two CTAs share an SM the rows
+// take the reflectors two at a time (compact WY of two), which halves the latency of the 8-lane
+// reductions that bound this streaming.
 
 // Sum over the 8 lanes of a row group (butterfly: every lane ends with the same bits).
 __device__ __forceinline__ dfloat df_group_sum(dfloat v) {
@@ -283,6 +285,68 @@ __device__ __forceinline__ void apply_reflector_df(dfloat (&y)[NS], const dfloat
     const int k = q + G * t;
     const dfloat vk = (k >= j && k < cols) ? v[min(k, cols - 1)] : df_zero();
     y[t] = df_fma(w, vk, y[t]);
+  }
+}
+
+// y <- y H_j H_{j+1} in one pass (the compact WY form of two reflectors, Schreiber and Van Loan
+// 1989): with a = tau_j (y . v_j) and b = tau_{j+1} (y . v_{j+1} - a c_j), c_j = v_j . v_{j+1},
+// the product is y - a v_j - b v_{j+1}. The two dot products share one pass over the row and
+// their 8-lane sums interleave, so each pair pays one reduction's latency instead of two.
+template <int NS>
+__device__ __forceinline__ void apply_reflector_pair_df(dfloat (&y)[NS], const dfloat* v,
+                                                        const dfloat* u, dfloat tj, dfloat tj1,
+                                                        dfloat cj, int j, int cols, int q) {
+  dfloat p1 = df_zero(), p2 = df_zero();
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    if (G * t + G - 1 < j || G * t >= cols) continue;
+    const int k = q + G * t;
+    const int kc = min(k, cols - 1);
+    const dfloat vk = (k >= j && k < cols) ? v[kc] : df_zero();
+    const dfloat uk = (k > j && k < cols) ? u[kc] : df_zero();
+    p1 = df_fma_acc(y[t], vk, p1);
+    p2 = df_fma_acc(y[t], uk, p2);
+  }
+  p1 = df_norm(p1);
+  p2 = df_norm(p2);
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const dfloat w1{__shfl_xor_sync(FULL, p1.hi, o), __shfl_xor_sync(FULL, p1.lo, o)};
+    const dfloat w2{__shfl_xor_sync(FULL, p2.hi, o), __shfl_xor_sync(FULL, p2.lo, o)};
+    p1 = df_add(p1, w1);
+    p2 = df_add(p2, w2);
+  }
+  const dfloat a = df_fma(p1, tj, df_zero());
+  const dfloat na = df_neg(a);
+  const dfloat nb = df_neg(df_fma(df_fma(na, cj, p2), tj1, df_zero()));
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    if (G * t + G - 1 < j || G * t >= cols) continue;
+    const int k = q + G * t;
+    const int kc = min(k, cols - 1);
+    const dfloat vk = (k >= j && k < cols) ? v[kc] : df_zero();
+    const dfloat uk = (k > j && k < cols) ? u[kc] : df_zero();
+    y[t] = df_fma(nb, uk, df_fma(na, vk, y[t]));
+  }
+}
+
+// c_j = v_j . v_{j+1} for the reflector pairs (j even, j + 1 < n) of a double-float image, into
+// the image's spare column `cols` of row j. One pair per group of 8 lanes; a warp stops only when
+// none of its groups has a pair, so every lane takes part in the shuffles.
+__device__ void pair_dots_df(dfloat* F, int ldF, int n, int cols) {
+  const int warp = threadIdx.x / 32, gid = threadIdx.x / G, q = threadIdx.x % G;
+  const int npairs = n / 2;
+  for (int base = 0; base < npairs; base += NGROUPS) {
+    if (base + warp * (32 / G) >= npairs) break;                // no pair for this warp
+    const int pr = base + gid;
+    const bool active = pr < npairs;
+    const int j = active ? 2 * pr : 0;
+    const dfloat* v = F + static_cast<size_t>(j) * ldF;
+    const dfloat* u = v + ldF;
+    dfloat c = df_zero();
+    for (int k = j + 1 + q; k < cols; k += G) c = df_fma_acc(v[k], u[k], c);
+    c = df_group_sum(df_norm(c));
+    if (active && q == 0) F[static_cast<size_t>(j) * ldF + cols] = c;
   }
 }
 
@@ -329,7 +393,9 @@ __device__ __forceinline__ void store_row_df(dfloat (&y)[NS], int i, bool active
   }
 }
 
-template <int NS>
+// PAIRS: the reflectors two at a time (apply_reflector_pair_df, with c_j in column s of row j);
+// otherwise one at a time.
+template <int NS, bool PAIRS>
 __device__ void stream_rows_df(const double* __restrict__ S, int n, int s, int r, int row0, int row1,
                                const dfloat* F, int ldF, const dfloat* tau, const dfloat* rdiag,
                                double* __restrict__ X, double* __restrict__ W) {
@@ -344,7 +410,14 @@ __device__ void stream_rows_df(const double* __restrict__ S, int n, int s, int r
       const int k = q + G * t;
       y[t] = (active && k < s) ? df_from(S[static_cast<size_t>(i) * s + k]) : df_zero();
     }
-    for (int j = 0; j < n; ++j)
+    int j = 0;
+    if constexpr (PAIRS) {
+      for (; j + 1 < n; j += 2) {
+        const dfloat* v = F + static_cast<size_t>(j) * ldF;
+        apply_reflector_pair_df<NS>(y, v, v + ldF, tau[j], tau[j + 1], v[s], j, s, q);
+      }
+    }
+    for (; j < n; ++j)
       apply_reflector_df<NS>(y, F + static_cast<size_t>(j) * ldF, tau[j], j, s, q);
     store_row_df<NS>(y, i, active, n, s, r, F, ldF, rdiag, X, W);
   }
@@ -440,14 +513,21 @@ __global__ void __launch_bounds__(THREADS, MINB)
   }
   if constexpr (DF) {
     image_to_df(F, n * ldF + 2 * n);
+    // Reflector pairs where two CTAs share an SM (128 registers a thread); at three CTAs per SM
+    // (80 registers) the pair form measured slower than one reflector at a time.
+    constexpr bool kPairs = MINB <= 2;
+    if constexpr (kPairs) {
+      pair_dots_df(reinterpret_cast<dfloat*>(F), ldF, n, s);    // into the spare column s
+      __syncthreads();
+    }
     const dfloat* Fd = reinterpret_cast<const dfloat*>(F);
     const dfloat* taud = Fd + static_cast<size_t>(n) * ldF;
     const dfloat* rdiagd = taud + n;
     if (tk.is_root) {
-      stream_rows_df<NS>(tk.Y, n, s, 0, row0, row1, Fd, ldF, taud, rdiagd, nullptr, tk.D);
+      stream_rows_df<NS, kPairs>(tk.Y, n, s, 0, row0, row1, Fd, ldF, taud, rdiagd, nullptr, tk.D);
       return;
     }
-    stream_rows_df<NS>(side ? tk.Z : tk.Y, n, s, r, row0, row1, Fd, ldF, taud, rdiagd,
+    stream_rows_df<NS, kPairs>(side ? tk.Z : tk.Y, n, s, r, row0, row1, Fd, ldF, taud, rdiagd,
                        side ? tk.XZ : tk.XY, side ? tk.WZ : tk.WY);
   } else {
     if (tk.is_root) {
