@@ -130,6 +130,8 @@ def test_compensated_sweep_random_inputs(hb, N, r, s, leaf):
 
 
 def test_compensated_batch_of_uneven_trees(hb):
+    # The second height holds 80 nodes of the four trees (up to 80 rows, s = 120): one side-kernel
+    # CTA per (node, side) at two CTAs per SM, whose double-float rows take the reflectors in pairs.
     cases = [(1024, 10, 30, 16), (777, 12, 40, 26), (129, 4, 12, 8), (2048, 40, 120, 64)]
     probs, refs = [], []
     for j, (N, r, s, leaf) in enumerate(cases):
