@@ -503,15 +503,7 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
   if (rc != HBS_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (precision == HBS_PREC_FP64_TC || precision == HBS_PREC_MIXED_COMPENSATED) {
-    static const int digits64 = [] {               // 7 (default) or 6 digits per entry
-      const char* v = getenv("HBS_OZ_DIGITS");
-      return (v && atoi(v) == 6) ? 6 : 7;
-    }();
-    static const int digits_mixed = [] {           // 5 (default) or 4 digits per entry
-      const char* v = getenv("HBS_MIXED_DIGITS");
-      return (v && atoi(v) == 4) ? 4 : 5;
-    }();
-    const int digits = precision == HBS_PREC_FP64_TC ? digits64 : digits_mixed;
+    const int digits = precision == HBS_PREC_FP64_TC ? 7 : 5;   // digits per entry
     // compensated products: one exponent per 64 x 64 block of A, planes in one orientation
     cudaError_t e = hbs::launch_sample_dense_oz(static_cast<const double*>(op->A), op->lda, op->N,
                                                 Omega, Psi, s, Y, Z, digits,
@@ -520,15 +512,10 @@ int hbs_sample_products(const hbs_operator* op, int32_t s, int32_t precision, co
     return ok();
   }
   if (precision != HBS_PREC_FP64) {
-    static const int kchunk = [] {                 // tuning override; 0 = split for occupancy
-      const char* v = getenv("HBS_TC_KCHUNK");
-      const int k = v ? atoi(v) : 0;
-      return (k >= 64 && k % 64 == 0) ? k : 0;
-    }();
     cudaError_t e = hbs::launch_sample_dense_tc(static_cast<const float*>(op->A), op->lda, op->N,
                                                 Omega, Psi, s, Y, Z,
                                                 precision == HBS_PREC_MIXED_BF16X3 ? 2 : 3,
-                                                kchunk, st);
+                                                0, st);   // reduction split chosen to fill the GPU
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core sampling");
     return ok();
   }

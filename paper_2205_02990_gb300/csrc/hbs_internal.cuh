@@ -139,8 +139,8 @@ cudaError_t sample_tc_inject(int bits);
 // Column tiling shared by the tensor-core products: s <= 128 as one tile of s rounded up to 32,
 // wider s as tiles of 128 (sample_tc.cu).
 void column_tiles(int s, int* BN, int* BNt);
-// FP64-class sampling by exact bfloat16 digit products on the tensor cores (sample_oz.cu):
-// A FP64 row-major (any lda >= N), digits = 4 .. 7, s <= 256, N <= 2^20. The scratch it grows
+// FP64-class sampling by exact FP16 digit products on the tensor cores (sample_oz.cu):
+// A FP64 row-major (any lda >= N), digits = 7 or 5, s <= 256, N <= 2^20. The scratch it grows
 // holds the device status word at its start.
 // shared_planes: one exponent per 64 x 64 block of A and its digit planes in one orientation,
 // read transposed by the product with A^* (half the split's work and scratch).

@@ -880,9 +880,7 @@ cudaError_t launch_sample_dense_oz(const double* A, int64_t lda, int64_t N, cons
   column_tiles(s, &BN, &BNt);
   if (oz_smem_bytes(digits, BN) > kMaxNodeSmemBytes) return cudaErrorInvalidValue;
   switch (digits) {
-    case 4: return launch_products<4>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
     case 5: return launch_products<5>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
-    case 6: return launch_products<6>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
     case 7: return launch_products<7>(A, lda, N, Om, Ps, s, Y, Z, shared_planes, st);
     default: return cudaErrorInvalidValue;
   }
